@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Demag evaluations per second of the tetrahedral FMM (Palmesi et al.) on GB300.
+
+One step = one demag_eval of the whole hot path (P2M, M2M, M2L, L2L, L2P, P2P,
+lumped H) over a batch of B magnetisation states of the workload mesh, inputs
+resident in HBM.  The metric counts (mesh, state) evaluations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision fp64|fp32|tf32|bf16x3] [--batch B]
+
+--impl reference times the CPU oracle (the plain FP64 FMM of oracle/) on the
+host cores, on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank evaluates its own batch on its own GPU
+(replicas, no data-path collective); value = all ranks' evals / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "demag evals/sec at rel-L2 1e-4 vs FP64: mixed+batched vs FP64 GPU FMM"
+UNIT = "evals/s"
+
+# Workloads.  sphere200k is the configuration the metric is quoted on
+# (radius-1 ball, ~200k quasi-uniform Delaunay tets, Gaussian unit M).
+WORKLOADS = {
+    "sphere200k": dict(mesh="sphere", h="SPHERE_200K_H", p=8, theta=0.5, leaf=32),
+    "cube8": dict(mesh="cube", n=8, p=4, theta=0.5, leaf=32),
+    "sphere30k": dict(mesh="sphere", h=0.095, p=6, theta=0.5, leaf=32),
+}
+
+
+def make_mesh(w):
+    from paper_1606_00247_gb300 import inputs
+
+    if w["mesh"] == "cube":
+        return inputs.unit_cube(w["n"])
+    h = getattr(inputs, w["h"]) if isinstance(w["h"], str) else w["h"]
+    return inputs.sphere(h=h)
+
+
+def make_M(nn, B, seed_offset=0):
+    from paper_1606_00247_gb300 import inputs
+
+    return inputs.gaussian_unit_m(nn, seed=inputs.MAG_SEED + 1 + seed_offset, batch=B)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP64 operations of one (target node, source tet) pair in pair_contract
+# (p2p.cuh), counted from the source: 12 subtractions, 4 norms (5 each),
+# 6 edges x 4, 4 faces x (h 5, triple product 14, 3 dots 15, denominator 7,
+# 3 edges x 14, face combination 12), M(r) 18  -> 48+24+4*95+18 = 470, plus
+# 4 sqrt, 6 log1p, 6 divisions and 4 atan2.
+P2P_FLOPS_PER_PAIR = 470
+
+
+def roofline_for(stats, steps_profiled, precision, peaks):
+    """Roofline of the dominant stage from the live per-stage CUDA-event times."""
+    ms = stats["stage_ms"]
+    dom = max(ms, key=lambda k: ms[k])
+    per_launch_ms = ms[dom] / max(1, stats["stage_launches"][dom])
+    launches_per_eval = stats["stage_launches"][dom] / max(1, steps_profiled)
+    B = stats["_batch"]
+    out = {"kernel": dom, "stage_ms_per_step": {k: v / max(1, steps_profiled) for k, v in ms.items()}}
+    if dom == "p2p":
+        flops = stats["n_p2p_pairs"] * P2P_FLOPS_PER_PAIR * B / launches_per_eval
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks.get("fp64_tflops")
+        src = "measured" if peak else "fallback (nominal GB300 FP64 1.25 TFLOP/s)"
+        peak = peak or 1.25
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": src,
+                    "note": "FP64 pipe; transcendentals not counted in achieved"})
+    else:
+        # other stages: report against HBM with the bytes they must move
+        nbytes = stats.get("_stage_bytes", {}).get(dom)
+        peak = peaks.get("hbm_gbs", 6800.0)
+        if nbytes:
+            achieved = nbytes / launches_per_eval / (per_launch_ms * 1e-3) / 1e9
+            out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None})
+        else:
+            out.update({"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(nodes, tets, w, M1, budget_s=20.0, frac=None):
+    """Time the oracle FMM on a bounded sample: full upward pass + a fraction of
+    the target leaves; extrapolate to evals/s for one state."""
+    import oracle
+
+    oracle.build()
+    tr = oracle.Tree(nodes, tets, w["leaf"], w["theta"])
+    ex = tr.export()
+    leaves = np.where((ex["cell_child"][:, 1] == 0) & (ex["cell_ranges"][:, 3] > ex["cell_ranges"][:, 2]))[0]
+    nthreads = oracle.max_threads()
+    t0 = time.perf_counter()
+    tr.fmm(M1, w["p"], target_leaves=np.zeros(0, np.int64))
+    t_up = time.perf_counter() - t0
+    if frac is None:
+        # probe with 0.5% of the leaves, then size the sample to the budget
+        probe = leaves[:: max(1, len(leaves) // max(1, len(leaves) // 200))]
+        t0 = time.perf_counter()
+        tr.fmm(M1, w["p"], target_leaves=probe)
+        t_probe = max(1e-6, time.perf_counter() - t0 - t_up)
+        per_leaf = t_probe / len(probe)
+        n = int(max(len(probe), min(len(leaves), (budget_s - t_up) / per_leaf)))
+        frac = n / len(leaves)
+    n = max(1, int(round(frac * len(leaves))))
+    sample = leaves[np.linspace(0, len(leaves) - 1, n).astype(np.int64)]
+    t0 = time.perf_counter()
+    tr.fmm(M1, w["p"], target_leaves=sample)
+    t_tot = time.perf_counter() - t0
+    t_down = max(0.0, t_tot - t_up)
+    t_eval = t_up + t_down * len(leaves) / len(sample)
+    return {"value": 1.0 / t_eval, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"plain CPU FMM, p={w['p']}, 1 state: full upward pass ({t_up:.2f} s) + "
+                      f"{len(sample)}/{len(leaves)} target leaves ({t_down:.2f} s), extrapolated to all leaves",
+            "seconds": t_up + t_down}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1606_00247_gb300 import build
+    from paper_1606_00247_gb300.api import Plan
+
+    build()
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    w = dict(WORKLOADS[args.workload])
+    if args.p:
+        w["p"] = args.p
+    nodes, tets = make_mesh(w)
+    B = args.batch
+    plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
+                near_mode=args.near_mode, max_batch=B, device=dev)
+    st0 = plan.stats()
+    M = torch.as_tensor(make_M(nodes.shape[0], B, seed_offset=rank), device=dev)
+    u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device=dev)
+    H = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.eval(M, u, H)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flushed between timed steps (outside the events)
+        ev[k][0].record(stream)
+        plan.eval(M, u, H)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    launches = plan.stats()["eval_launches"] * args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * B * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside)
+    Mh = make_M(nodes.shape[0], B, seed_offset=rank)
+    plan.eval_host(Mh)
+    t_e2e = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        plan.eval_host(Mh)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_value = world * B * args.steps / sum(t_e2e)
+
+    # live per-stage timing pass (CUDA events on the eval stream, inside the library)
+    prof = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
+                near_mode=args.near_mode, max_batch=B, device=dev, profile=True)
+    for _ in range(2):
+        prof.eval(M, u, H)
+    prof.reset_timers()
+    nprof = max(2, min(args.steps, 5))
+    for _ in range(nprof):
+        flush.zero_()
+        prof.eval(M, u, H)
+    pst = prof.stats()
+    pst["_batch"] = B
+    roof = roofline_for(pst, nprof, args.precision, measured_peaks())
+    prof.close()
+
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic (seeded Delaunay ball, Gaussian unit nodal M)",
+        "config": {"workload": args.workload, "n_tets": st0["n_tets"], "n_nodes": st0["n_nodes"],
+                   "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_gpu": B,
+                   "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}", "n_cells": st0["n_cells"], "n_m2l": st0["n_m2l"],
+                   "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
+                   "plan_ms": st0["plan_ms"]},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Mh.nbytes),
+                "d2h_bytes_per_step": int(B * nodes.shape[0] * 4 * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(nodes, tets, w, make_M(nodes.shape[0], 1)[0], budget_s=args.cpu_budget)
+    return out
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    w = dict(WORKLOADS[args.workload])
+    if args.p:
+        w["p"] = args.p
+    nodes, tets = make_mesh(w)
+    M1 = make_M(nodes.shape[0], 1)[0]
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    first = oracle_sample(nodes, tets, w, M1, budget_s=budget)
+    frac = None
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = first if k == 0 else oracle_sample(nodes, tets, w, M1, frac=frac)
+        if frac is None:
+            frac = float(r["sample"].split(" + ")[1].split(" ")[0].split("/")[0]) / float(
+                r["sample"].split("/")[1].split(" ")[0])
+        if k >= args.warmup:
+            vals.append(r["value"])
+    value = float(np.mean(vals))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"]},
+            "cpu_baseline": {"kind": "oracle", "cores": first["cores"], "sample": first["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere200k", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"])
+    ap.add_argument("--near-mode", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * demag.h -- C ABI of the GB300 tetrahedral-FMM demagnetisation library
+ * (libdemag.so).
+ *
+ * Operation (Palmesi et al., Sec. 1, Eq. (1)-(2)): for a tetrahedral mesh whose
+ * tets carry an affine (P1, nodal) magnetisation M, compute at every node
+ *     u(r_i) = 1/(4 pi) sum_j int_{Omega_j} M(r') . grad'(1/|r_i - r'|) dr'
+ * by the fast multipole method of Sec. 2-3: analytic near field over source
+ * tets (P2P, Sec. 2.1), exact tet moments (P2M, Sec. 2.2 Eq. expCoeffs),
+ * M2M / M2L / L2L on an octree (Sec. 2 steps 2-4, Sec. 2.3) and L2P (step 5),
+ * with the octree, multipole acceptance criterion and dual tree traversal of
+ * Sec. 3.1-3.3.  H is the mass-lumped field -grad u (Sec. 4.1, "mass lumping
+ * was used for the computation of the B-field").
+ *
+ * Units: lengths in mesh units, M in A/m, u in A, H in A/m; no mu0.
+ * Sign: H = -grad u, so H = -M/3 inside a uniformly magnetised ball.
+ *
+ * Error behaviour: no call throws across the ABI; every call returns a
+ * demag_status.  demag_last_error() gives a thread-local message for the last
+ * failing call.  On error, outputs are unspecified; a plan stays valid unless
+ * the status is DEMAG_ERR_CUDA or DEMAG_ERR_OUT_OF_MEMORY.
+ *
+ * Threads: a plan is read-only during demag_eval except for its internal
+ * workspace, so concurrent demag_eval calls on ONE plan must be serialised by
+ * the caller (they share the workspace); different plans are independent.
+ */
+#ifndef DEMAG_H
+#define DEMAG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct demag_plan_s* demag_plan;
+
+typedef enum {
+  DEMAG_OK = 0,
+  DEMAG_ERR_INVALID_ARG = 1,    /* bad pointer, size, index, p, leaf or theta     */
+  DEMAG_ERR_DEGENERATE_TET = 2, /* |vol| < 1e-14 * (longest edge)^3               */
+  DEMAG_ERR_OUT_OF_MEMORY = 3,  /* device allocation failed                        */
+  DEMAG_ERR_CUDA = 4,           /* a CUDA runtime call failed                      */
+  DEMAG_ERR_TIMEOUT = 5,        /* a bounded device wait expired                   */
+  DEMAG_ERR_UNSUPPORTED = 6     /* option combination not built                    */
+} demag_status;
+
+/* Arithmetic of the evaluation.  DEMAG_FP64: every stage in FP64 (the
+ * reference path).  Mixed modes keep the near-field integrals in FP64 (they are
+ * computed once, at plan time, when near_mode = 1) and run moments, M2M, M2L,
+ * L2L, L2P and the near-field application in FP32 arithmetic (FP32 CUDA
+ * cores, TF32 tensor cores, or split-BF16 x3 tensor cores for M2L), with the
+ * expansion coefficients scaled per octree level. */
+typedef enum {
+  DEMAG_FP64 = 0,
+  DEMAG_MIXED_FP32 = 1,
+  DEMAG_MIXED_TF32 = 2,
+  DEMAG_MIXED_BF16X3 = 3
+} demag_precision;
+
+typedef struct {
+  int p;               /* Taylor order, |n| <= p (Sec. 2.2); 1..12        */
+  int leaf_size;       /* split a cell holding more tets than this        */
+  double theta;        /* MAC: accept iff (r_T + r_S) < theta |c_T - c_S| */
+  int precision;       /* demag_precision                                  */
+  int near_mode;       /* 0: near field integrated at every eval (FP64);
+                          1: near-field coefficients W precomputed in FP64
+                             at plan time and applied at eval (Sec. 3.4 stores
+                             the direct-interaction coefficients)            */
+  int max_batch;       /* largest batch B a demag_eval will be given       */
+  int autotune;        /* reserved, must be 0                              */
+  int profile;         /* 1: time every stage of demag_eval with CUDA events
+                          on the eval stream (adds one synchronisation per
+                          call); read with demag_plan_stats                  */
+} demag_options;
+
+/* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
+ * autotune=0, profile=0. */
+void demag_options_default(demag_options* opt);
+
+/* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and
+ * dual tree traversal into M2L and P2P lists, tet geometry, exact-moment
+ * operators and, for near_mode=1, the near-field coefficients.
+ *   nodes : n_nodes x 3 doubles, row-major (x,y,z).  Host or device pointer.
+ *   tets  : n_tets x 4 int32, 0-based node indices, either orientation.
+ *           Host or device pointer.
+ *   p, leaf_size, theta override the corresponding fields of *opt.
+ *   opt   : may be NULL (defaults).
+ *   out   : receives the plan.  The plan copies nodes and tets; the caller
+ *           keeps ownership of its arrays.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL pointers, n_nodes<4, n_tets<1, index out
+ * of range, p outside 1..12, leaf_size<1, theta<=0 or non-finite, max_batch<1),
+ * DEMAG_ERR_DEGENERATE_TET, DEMAG_ERR_OUT_OF_MEMORY, DEMAG_ERR_CUDA.
+ * theta >= 1 is accepted; demag_last_error() then warns that expansions may
+ * not converge.  Runs on the current CUDA device, on its own stream, and
+ * synchronises before returning. */
+demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, int p,
+                               int leaf_size, double theta, const demag_options* opt, demag_plan* out);
+
+/* Evaluate u (and H) for `batch` magnetisation states (Sec. 2 steps 1-5 + P2P,
+ * Sec. 4.1 mass lumping).
+ *   M : batch x n_nodes x 3 doubles (state-major), nodal magnetisation.
+ *   u : batch x n_nodes doubles, output.
+ *   H : batch x n_nodes x 3 doubles, output; may be NULL.
+ *   M, u, H must be all device pointers or all host pointers.  With device
+ *   pointers the call is asynchronous on `cuda_stream` (a cudaStream_t; NULL =
+ *   the legacy default stream).  With host pointers the inputs are copied to
+ *   the device, and the call returns after the outputs are back in host
+ *   memory.  batch must be in 1..max_batch.
+ * Nodes that belong to no tet get their potential, and H = 0. */
+demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream);
+
+demag_status demag_plan_destroy(demag_plan plan);
+
+/* Stages of demag_eval, for the per-stage timers. */
+enum {
+  DEMAG_STAGE_GATHER = 0, /* M to the sorted, state-innermost layout          */
+  DEMAG_STAGE_P2M = 1,    /* exact tet moments of the source leaves           */
+  DEMAG_STAGE_M2M = 2,
+  DEMAG_STAGE_M2L = 3,
+  DEMAG_STAGE_L2L = 4,
+  DEMAG_STAGE_L2P = 5,
+  DEMAG_STAGE_NEAR_PREP = 6, /* per-tet, per-state records of the near field */
+  DEMAG_STAGE_P2P = 7,
+  DEMAG_STAGE_H = 8,         /* mass-lumped H and the output layout           */
+  DEMAG_N_STAGES = 9
+};
+
+typedef struct {
+  int64_t n_nodes, n_tets;
+  int64_t n_cells, n_leaves, n_levels;
+  int64_t n_m2l;         /* M2L cell pairs                                   */
+  int64_t n_p2p;         /* P2P leaf pairs                                   */
+  int64_t n_p2p_pairs;   /* (target node, source tet) pairs in the near field */
+  int64_t n_near_cols;   /* stored (target node, source node) coefficients   */
+  int64_t device_bytes;  /* device memory held by the plan                   */
+  double lo[3], side, scale; /* bounding cube and Morton scale              */
+  double plan_ms;        /* wall time of demag_plan_create                    */
+  int p, leaf_size, precision, near_mode, max_batch;
+  double theta;
+  int64_t eval_launches;           /* kernels launched by the last demag_eval */
+  int64_t n_evals_profiled;        /* evals accumulated in stage_ms          */
+  double stage_ms[DEMAG_N_STAGES]; /* summed per-stage device time (profile=1) */
+  int64_t stage_launches[DEMAG_N_STAGES];
+} demag_stats;
+
+demag_status demag_plan_stats(demag_plan plan, demag_stats* out);
+/* Zero the per-stage timers. */
+demag_status demag_plan_reset_timers(demag_plan plan);
+
+/* Host copies of the tree and lists, for bit-exact checks.  Every pointer may
+ * be NULL; sizes from demag_plan_stats.  Keys and permutations follow the
+ * readings of Sec. 3.1 documented with the oracle: 63-bit Morton keys (x in
+ * bit 3b, y in 3b+1, z in 3b+2) of the nodes and of the tet centroids
+ * ((v0+v1)+(v2+v3))*0.25 over the cube [lo, lo+side), sorted by
+ * (key, original index); cells level by level in ascending key prefix. */
+typedef struct {
+  uint64_t* node_key;    /* n_nodes, original node order            */
+  uint64_t* tet_key;     /* n_tets, original tet order              */
+  int64_t* node_perm;    /* n_nodes, sorted position -> node         */
+  int64_t* tet_perm;     /* n_tets, sorted position -> tet           */
+  int32_t* cell_level;   /* n_cells                                  */
+  uint64_t* cell_prefix; /* n_cells, key >> 3*(21-level)             */
+  int64_t* cell_ranges;  /* n_cells x 4: tet begin,end, node begin,end (sorted positions) */
+  int64_t* cell_parent;  /* n_cells, -1 for the root                 */
+  int64_t* cell_child;   /* n_cells x 2: first child, child count    */
+  double* cell_centre;   /* n_cells x 3                              */
+  double* cell_radius;   /* n_cells x 2: source radius, target radius */
+  int64_t* m2l_off;      /* n_cells + 1, CSR by target cell          */
+  int64_t* m2l_src;      /* n_m2l, ascending within a target         */
+  int64_t* p2p_off;      /* n_cells + 1                              */
+  int64_t* p2p_src;      /* n_p2p                                    */
+} demag_tree_export;
+
+demag_status demag_plan_export_tree(demag_plan plan, demag_tree_export* out);
+
+const char* demag_status_string(demag_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* demag_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

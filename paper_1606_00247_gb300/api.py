@@ -1,0 +1,127 @@
+"""Python face of the C ABI: a Plan object over demag_plan_create / demag_eval.
+
+PyTorch supplies device memory and streams; every stage runs in libdemag.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PREC = {"fp64": L.DEMAG_FP64, "fp32": L.DEMAG_MIXED_FP32, "tf32": L.DEMAG_MIXED_TF32,
+         "bf16x3": L.DEMAG_MIXED_BF16X3}
+
+
+def _as_f64(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
+
+
+def _as_i32(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.int32).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.int32), device=device)
+
+
+class Plan:
+    """Tree, lists and operators of one mesh (demag_plan_create)."""
+
+    def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
+                 device="cuda", profile=False):
+        self.device = torch.device(device)
+        nodes_t = _as_f64(nodes, self.device)
+        tets_t = _as_i32(tets, self.device)
+        self.n_nodes, self.n_tets = int(nodes_t.shape[0]), int(tets_t.shape[0])
+        opt = L.demag_options_default()
+        opt.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        opt.near_mode = int(near_mode)
+        opt.max_batch = int(max_batch)
+        opt.profile = int(bool(profile))
+        with torch.cuda.device(self.device):
+            st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
+                                        int(leaf_size), float(theta), opt)
+        L.check(st, "demag_plan_create")
+        self._h = h
+        self.p, self.max_batch = int(p), int(max_batch)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            L.demag_plan_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def eval(self, M, u=None, H=None, with_H=True, stream=None):
+        """u (B, N_n) and H (B, N_n, 3) for M (B, N_n, 3) or (N_n, 3) on the device."""
+        M = _as_f64(M, self.device)
+        squeeze = M.dim() == 2
+        if squeeze:
+            M = M.unsqueeze(0)
+        B = int(M.shape[0])
+        if u is None:
+            u = torch.empty((B, self.n_nodes), dtype=torch.float64, device=self.device)
+        if with_H and H is None:
+            H = torch.empty((B, self.n_nodes, 3), dtype=torch.float64, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = L.demag_eval(self._h, M.data_ptr(), B, u.data_ptr(), H.data_ptr() if with_H else None, s.cuda_stream)
+        L.check(st, "demag_eval")
+        if squeeze:
+            return u[0], (H[0] if with_H else None)
+        return u, (H if with_H else None)
+
+    def eval_host(self, M: np.ndarray, with_H=True):
+        """Same call with host (numpy) buffers: the library copies in and out."""
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        squeeze = M.ndim == 2
+        if squeeze:
+            M = M[None]
+        B = M.shape[0]
+        u = np.empty((B, self.n_nodes))
+        H = np.empty((B, self.n_nodes, 3)) if with_H else None
+        with torch.cuda.device(self.device):
+            st = L.demag_eval(self._h, M.ctypes.data, B, u.ctypes.data, H.ctypes.data if with_H else None, None)
+        L.check(st, "demag_eval")
+        if squeeze:
+            return u[0], (H[0] if with_H else None)
+        return u, H
+
+    def stats(self) -> dict:
+        st, s = L.demag_plan_stats(self._h)
+        L.check(st, "demag_plan_stats")
+        out = {f: getattr(s, f) for f, _ in s._fields_}
+        out["lo"] = list(s.lo)
+        out["stage_ms"] = dict(zip(L.STAGES, list(s.stage_ms)))
+        out["stage_launches"] = dict(zip(L.STAGES, list(s.stage_launches)))
+        return out
+
+    def reset_timers(self):
+        L.check(L.demag_plan_reset_timers(self._h), "demag_plan_reset_timers")
+
+    def export_tree(self) -> dict:
+        s = self.stats()
+        nn, nt, nc = s["n_nodes"], s["n_tets"], s["n_cells"]
+        arrs = dict(
+            node_key=np.zeros(nn, np.uint64), tet_key=np.zeros(nt, np.uint64), node_perm=np.zeros(nn, np.int64),
+            tet_perm=np.zeros(nt, np.int64), cell_level=np.zeros(nc, np.int32), cell_prefix=np.zeros(nc, np.uint64),
+            cell_ranges=np.zeros((nc, 4), np.int64), cell_parent=np.zeros(nc, np.int64),
+            cell_child=np.zeros((nc, 2), np.int64), cell_centre=np.zeros((nc, 3)), cell_radius=np.zeros((nc, 2)),
+            m2l_off=np.zeros(nc + 1, np.int64), m2l_src=np.zeros(max(s["n_m2l"], 1), np.int64),
+            p2p_off=np.zeros(nc + 1, np.int64), p2p_src=np.zeros(max(s["n_p2p"], 1), np.int64))
+        ex = L.demag_tree_export()
+        for k, a in arrs.items():
+            setattr(ex, k, a.ctypes.data)
+        L.check(L.demag_plan_export_tree(self._h, ex), "demag_plan_export_tree")
+        arrs["m2l_src"] = arrs["m2l_src"][: s["n_m2l"]]
+        arrs["p2p_src"] = arrs["p2p_src"][: s["n_p2p"]]
+        return arrs

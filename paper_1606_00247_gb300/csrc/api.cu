@@ -1,0 +1,280 @@
+// api.cu -- the extern "C" boundary of libdemag.so (include/demag.h).
+// No exception crosses it: every entry point catches and returns a status.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace demag {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+[[noreturn]] void fail(demag_status s, const std::string& msg) { throw Error{s, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();
+  demag_status s = (e == cudaErrorMemoryAllocation) ? DEMAG_ERR_OUT_OF_MEMORY : DEMAG_ERR_CUDA;
+  throw Error{s, std::string(what) + " failed: " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) +
+                     ")"};
+}
+
+StageClock::StageClock(Plan& P_, cudaStream_t s_) : P(P_), s(s_), on(P_.opt.profile != 0) {
+  if (on)
+    for (auto& e : ev) DM_CUDA(cudaEventCreate(&e));
+}
+StageClock::~StageClock() {
+  if (on)
+    for (auto& e : ev) cudaEventDestroy(e);
+}
+void StageClock::begin(int stage) {
+  cur = stage;
+  used[stage] = true;
+  if (on) DM_CUDA(cudaEventRecord(ev[2 * stage], s));
+}
+void StageClock::end() {
+  if (on) DM_CUDA(cudaEventRecord(ev[2 * cur + 1], s));
+}
+void StageClock::finish() {
+  int64_t total = 0;
+  for (int k = 0; k < DEMAG_N_STAGES; k++) total += launches[k];
+  P.eval_launches = total;
+  if (!on) return;
+  DM_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < DEMAG_N_STAGES; k++) {
+    if (!used[k]) continue;
+    float ms = 0;
+    DM_CUDA(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    P.stage_ms[k] += ms;
+    P.stage_launches[k] += launches[k];
+  }
+  P.n_evals_profiled++;
+}
+
+void dfree_all(Plan& P) {
+  for (auto& b : P.bufs) cudaFree(b.ptr);
+  P.bufs.clear();
+  P.device_bytes = 0;
+}
+
+template <class F>
+static demag_status guarded(F&& f) {
+  try {
+    f();
+    return DEMAG_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return DEMAG_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    set_last_error("unexpected internal error");
+    return DEMAG_ERR_CUDA;
+  }
+}
+
+template <class Dst, class Src>
+static void copy_convert(Dst* dst, const Src* src_dev, int64_t n, cudaStream_t s) {
+  if (!dst || n <= 0) return;
+  std::vector<Src> h(n);
+  DM_CUDA(cudaMemcpyAsync(h.data(), src_dev, n * sizeof(Src), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; i++) dst[i] = (Dst)h[i];
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" {
+
+void demag_options_default(demag_options* o) {
+  if (!o) return;
+  o->p = 4;
+  o->leaf_size = 32;
+  o->theta = 0.5;
+  o->precision = DEMAG_FP64;
+  o->near_mode = 0;
+  o->max_batch = 1;
+  o->autotune = 0;
+  o->profile = 0;
+}
+
+demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, int p,
+                               int leaf_size, double theta, const demag_options* opt, demag_plan* out) {
+  set_last_error("");
+  if (out) *out = nullptr;
+  demag_plan_s* P = nullptr;
+  demag_status st = guarded([&] {
+    if (!nodes || !tets || !out) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
+    if (n_nodes < 4 || n_tets < 1) fail(DEMAG_ERR_INVALID_ARG, "need n_nodes >= 4 and n_tets >= 1");
+    if (n_nodes > INT32_MAX / 4 || n_tets > INT32_MAX / 4) fail(DEMAG_ERR_INVALID_ARG, "mesh too large");
+    demag_options o;
+    demag_options_default(&o);
+    if (opt) o = *opt;
+    o.p = p;
+    o.leaf_size = leaf_size;
+    o.theta = theta;
+    if (o.p < 1 || o.p > MAX_P) fail(DEMAG_ERR_INVALID_ARG, "p must be in 1..12");
+    if (o.leaf_size < 1) fail(DEMAG_ERR_INVALID_ARG, "leaf_size must be >= 1");
+    if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
+    if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
+    if (o.autotune != 0) fail(DEMAG_ERR_UNSUPPORTED, "autotune is reserved");
+    if (o.precision != DEMAG_FP64 || o.near_mode != 0)
+      fail(DEMAG_ERR_UNSUPPORTED, "only precision=DEMAG_FP64 with near_mode=0 is built in this version");
+    P = new demag_plan_s();
+    P->opt = o;
+    P->p = o.p;
+    P->nc = ncoef_of(o.p);
+    P->nn = n_nodes;
+    P->nt = n_tets;
+    DM_CUDA(cudaGetDevice(&P->device));
+    DM_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    build_plan(*P, nodes, tets);
+    if (o.theta >= 1.0)
+      set_last_error("warning: theta >= 1, multipole expansions may not converge for accepted pairs");
+    *out = P;
+  });
+  if (st != DEMAG_OK && P) {
+    destroy_workspace(*P);
+    dfree_all(*P);
+    if (P->stream) cudaStreamDestroy(P->stream);
+    delete P;
+  }
+  return st;
+}
+
+demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream) {
+  return guarded([&] {
+    if (!plan || !M || !u) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
+    if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
+    eval_fp64(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
+  });
+}
+
+demag_status demag_plan_destroy(demag_plan plan) {
+  if (!plan) return DEMAG_ERR_INVALID_ARG;
+  return guarded([&] {
+    cudaStreamSynchronize(plan->stream);
+    destroy_workspace(*plan);
+    dfree_all(*plan);
+    cudaStreamDestroy(plan->stream);
+    delete plan;
+  });
+}
+
+demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
+  if (!plan || !o) return DEMAG_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->n_nodes = plan->nn;
+  o->n_tets = plan->nt;
+  o->n_cells = plan->ncells;
+  o->n_leaves = plan->nleaves;
+  o->n_levels = plan->nlevels;
+  o->n_m2l = plan->n_m2l;
+  o->n_p2p = plan->n_p2p;
+  o->n_p2p_pairs = plan->n_p2p_pairs;
+  o->n_near_cols = 0;
+  o->device_bytes = plan->device_bytes;
+  for (int a = 0; a < 3; a++) o->lo[a] = plan->lo[a];
+  o->side = plan->side;
+  o->scale = plan->scale;
+  o->plan_ms = plan->plan_ms;
+  o->p = plan->p;
+  o->leaf_size = plan->opt.leaf_size;
+  o->precision = plan->opt.precision;
+  o->near_mode = plan->opt.near_mode;
+  o->max_batch = plan->opt.max_batch;
+  o->theta = plan->opt.theta;
+  o->eval_launches = plan->eval_launches;
+  o->n_evals_profiled = plan->n_evals_profiled;
+  for (int k = 0; k < DEMAG_N_STAGES; k++) {
+    o->stage_ms[k] = plan->stage_ms[k];
+    o->stage_launches[k] = plan->stage_launches[k];
+  }
+  return DEMAG_OK;
+}
+
+demag_status demag_plan_reset_timers(demag_plan plan) {
+  if (!plan) return DEMAG_ERR_INVALID_ARG;
+  for (int k = 0; k < DEMAG_N_STAGES; k++) {
+    plan->stage_ms[k] = 0;
+    plan->stage_launches[k] = 0;
+  }
+  plan->n_evals_profiled = 0;
+  return DEMAG_OK;
+}
+
+demag_status demag_plan_export_tree(demag_plan plan, demag_tree_export* o) {
+  if (!plan || !o) return DEMAG_ERR_INVALID_ARG;
+  return guarded([&] {
+    Plan& P = *plan;
+    cudaStream_t s = P.stream;
+    const int64_t nc = P.ncells;
+    copy_convert(o->node_key, P.node_key, P.nn, s);
+    copy_convert(o->tet_key, P.tet_key, P.nt, s);
+    copy_convert(o->node_perm, P.node_perm, P.nn, s);
+    copy_convert(o->tet_perm, P.tet_perm, P.nt, s);
+    copy_convert(o->cell_level, P.cell_level, nc, s);
+    copy_convert(o->cell_prefix, P.cell_prefix, nc, s);
+    copy_convert(o->cell_parent, P.cell_parent, nc, s);
+    copy_convert(o->cell_centre, P.cell_centre, 3 * nc, s);
+    copy_convert(o->m2l_off, P.m2l_off, nc + 1, s);
+    copy_convert(o->m2l_src, P.m2l_src, P.n_m2l, s);
+    copy_convert(o->p2p_off, P.p2p_off, nc + 1, s);
+    copy_convert(o->p2p_src, P.p2p_src, P.n_p2p, s);
+    if (o->cell_ranges) {
+      std::vector<int4> h(nc);
+      DM_CUDA(cudaMemcpyAsync(h.data(), P.cell_range, nc * sizeof(int4), cudaMemcpyDeviceToHost, s));
+      DM_CUDA(cudaStreamSynchronize(s));
+      for (int64_t c = 0; c < nc; c++) {
+        o->cell_ranges[4 * c] = h[c].x;
+        o->cell_ranges[4 * c + 1] = h[c].y;
+        o->cell_ranges[4 * c + 2] = h[c].z;
+        o->cell_ranges[4 * c + 3] = h[c].w;
+      }
+    }
+    if (o->cell_child) {
+      std::vector<int32_t> c0(nc), cn(nc);
+      DM_CUDA(cudaMemcpyAsync(c0.data(), P.cell_child0, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      DM_CUDA(cudaMemcpyAsync(cn.data(), P.cell_nchild, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      DM_CUDA(cudaStreamSynchronize(s));
+      for (int64_t c = 0; c < nc; c++) {
+        o->cell_child[2 * c] = c0[c];
+        o->cell_child[2 * c + 1] = cn[c];
+      }
+    }
+    if (o->cell_radius) {
+      std::vector<double> rs(nc), rt(nc);
+      DM_CUDA(cudaMemcpyAsync(rs.data(), P.cell_rsrc, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DM_CUDA(cudaMemcpyAsync(rt.data(), P.cell_rtgt, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DM_CUDA(cudaStreamSynchronize(s));
+      for (int64_t c = 0; c < nc; c++) {
+        o->cell_radius[2 * c] = rs[c];
+        o->cell_radius[2 * c + 1] = rt[c];
+      }
+    }
+  });
+}
+
+const char* demag_status_string(demag_status s) {
+  switch (s) {
+    case DEMAG_OK: return "ok";
+    case DEMAG_ERR_INVALID_ARG: return "invalid argument";
+    case DEMAG_ERR_DEGENERATE_TET: return "degenerate tetrahedron";
+    case DEMAG_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case DEMAG_ERR_CUDA: return "CUDA error";
+    case DEMAG_ERR_TIMEOUT: return "device wait timed out";
+    case DEMAG_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+const char* demag_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// common.cuh -- internal declarations shared by the translation units of
+// libdemag.so: the plan structure, error plumbing, multi-index helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/demag.h"
+
+namespace demag {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+  demag_status status;
+  std::string msg;
+};
+void set_last_error(const std::string& msg);
+[[noreturn]] void fail(demag_status s, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define DM_CUDA(x) ::demag::check_cuda((x), #x, __FILE__, __LINE__)
+#define DM_LAUNCH(what) ::demag::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+
+// Octree constants (Sec. 3.1 reading): 21 bits per axis, cells split up to level 20.
+constexpr int KEY_BITS = 21;
+constexpr int MAX_LEVEL = 20;
+constexpr int MAX_P = 12;
+constexpr int MAX_NCOEF = (MAX_P + 1) * (MAX_P + 2) * (MAX_P + 3) / 6;  // 455
+
+__host__ __device__ inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Graded multi-index order: total degree t ascending; within t, n_x descending,
+// then n_z ascending.  Index of (a,b,c):
+//   t(t+1)(t+2)/6 + (b+c)(b+c+1)/2 + c,  t = a+b+c.
+__host__ __device__ inline int mi_index(int a, int b, int c) {
+  int t = a + b + c, j = b + c;
+  return t * (t + 1) * (t + 2) / 6 + j * (j + 1) / 2 + c;
+}
+__host__ __device__ inline void mi_decode(int idx, int& a, int& b, int& c) {
+  int t = 0;
+  while ((t + 1) * (t + 2) * (t + 3) / 6 <= idx) t++;
+  int r = idx - t * (t + 1) * (t + 2) / 6;
+  int j = 0;
+  while ((j + 1) * (j + 2) / 2 <= r) j++;
+  c = r - j * (j + 1) / 2;
+  b = j - c;
+  a = t - j;
+}
+
+// ---------------------------------------------------------------------------
+// per-tet record used by the near field (sorted tet order, 66 doubles):
+//   [0..11]  vertices v0..v3
+//   [12..23] unit outward face normals n_F (face F opposite vertex F)
+//   [24..59] unit outward in-plane edge normals m_{F,e}, edge e of face F
+//   [60..65] edge lengths of the 6 edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
+// Tets are stored positively oriented (vertices 2,3 swapped when needed) so the
+// faces have the fixed counter-clockwise vertex orders below.
+// ---------------------------------------------------------------------------
+constexpr int TET_GEO = 66;
+// per-tet, per-state record for the on-the-fly near field (56 doubles):
+//   [0..2] M(v0)  [3..11] J = dM/dx (row a = component)  [12..23] alpha_{F,e}
+//   [24..35] beta_{F,e}  [36..47] mu_{F,e}  [48..51] gamma_F  [52..55] eps_F
+constexpr int TET_STATE = 56;
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct Plan;
+struct Workspace;
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // plan-build stream
+  demag_options opt{};
+  int p = 4, nc = 35, nc1 = 20;   // order, ncoef(p), ncoef(p-1)
+  int64_t nn = 0, nt = 0;
+  double lo[3] = {0, 0, 0}, side = 0, scale = 0;
+  double plan_ms = 0;
+
+  // sorted geometry
+  double* nodes_s = nullptr;      // nn x 3 (sorted node order)
+  int32_t* tets_s = nullptr;      // nt x 4 sorted node ids, positively oriented
+  int32_t* node_perm = nullptr;   // sorted -> original
+  int32_t* tet_perm = nullptr;
+  uint64_t* node_key = nullptr;   // original order
+  uint64_t* tet_key = nullptr;
+  double* tet_geo = nullptr;      // nt x TET_GEO
+  double* tet_grad = nullptr;     // nt x 12 gradients of the barycentric coords
+  double* tet_vol = nullptr;      // nt, |vol|
+
+  // cells
+  int64_t ncells = 0;
+  int nlevels = 0;
+  std::vector<int64_t> level_start;  // host, nlevels+1
+  uint64_t* cell_prefix = nullptr;
+  int32_t* cell_level = nullptr;
+  int4* cell_range = nullptr;       // tet begin,end, node begin,end
+  int32_t* cell_parent = nullptr;
+  int32_t* cell_child0 = nullptr;
+  int32_t* cell_nchild = nullptr;
+  double* cell_centre = nullptr;    // ncells x 3
+  double* cell_rsrc = nullptr;
+  double* cell_rtgt = nullptr;
+  int64_t nleaves = 0;
+
+  // interaction lists (CSR by target cell)
+  int64_t n_m2l = 0, n_p2p = 0, n_p2p_pairs = 0;
+  int64_t* m2l_off = nullptr;
+  int32_t* m2l_src = nullptr;
+  int64_t* p2p_off = nullptr;
+  int32_t* p2p_src = nullptr;
+  // host copies used for launch shapes
+  std::vector<int32_t> h_m2l_targets;  // cells with non-empty M2L lists
+  std::vector<int32_t> h_p2p_targets;  // leaves with nodes and non-empty P2P lists
+  int32_t* m2l_targets = nullptr;      // device copies of the two lists above
+  int32_t* p2p_targets = nullptr;
+
+  // targets
+  int32_t* node_leaf = nullptr;     // sorted node -> leaf cell
+  // source leaves: support nodes (unique nodes of the leaf's tets)
+  int64_t n_sup = 0;
+  int64_t* sup_off = nullptr;       // ncells + 1
+  int32_t* sup_node = nullptr;      // n_sup sorted node ids
+  int32_t* tet_col = nullptr;       // nt x 4: column of each vertex in its leaf's support
+  std::vector<int32_t> h_src_leaves;// leaves holding tets
+  int32_t* src_leaves = nullptr;
+  double* Ghat = nullptr;           // n_sup x nc1 : int lambda_k y^m/m! over the leaf's tets at that node
+
+  // node -> incident tets (for lumped H)
+  int64_t* nt_off = nullptr;        // nn + 1
+  int32_t* nt_tet = nullptr;        // 4 nt, sorted tet ids
+
+  std::vector<DevBuf> bufs;
+  int64_t device_bytes = 0;
+  Workspace* ws = nullptr;
+
+  // per-stage timers (opt.profile) and launch counts
+  double stage_ms[DEMAG_N_STAGES] = {};
+  int64_t stage_launches[DEMAG_N_STAGES] = {};
+  int64_t n_evals_profiled = 0;
+  int64_t eval_launches = 0;
+};
+
+// Records CUDA events around the stages of one demag_eval when profiling is on
+// and counts kernel launches always.
+struct StageClock {
+  Plan& P;
+  cudaStream_t s;
+  bool on;
+  cudaEvent_t ev[2 * DEMAG_N_STAGES];
+  int launches[DEMAG_N_STAGES] = {};
+  bool used[DEMAG_N_STAGES] = {};
+  int cur = -1;
+  StageClock(Plan& P_, cudaStream_t s_);
+  ~StageClock();
+  void begin(int stage);
+  void end();
+  void launched(int n = 1) { launches[cur] += n; }
+  void finish();  // synchronises on the last event and accumulates
+};
+
+template <class T>
+T* dalloc(Plan& P, size_t n) {
+  void* p = nullptr;
+  size_t bytes = n * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(DEMAG_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  P.bufs.push_back({p, bytes});
+  P.device_bytes += (int64_t)bytes;
+  return (T*)p;
+}
+void dfree_all(Plan& P);
+
+// stages (defined in plan.cu / fmm.cu / p2p.cu / eval.cu)
+void build_plan(Plan& P, const double* nodes, const int32_t* tets);
+void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
+void destroy_workspace(Plan& P);
+
+// near field (p2p.cu)
+void build_tet_geometry(Plan& P);
+void launch_tet_state(Plan& P, const double* Ms, int B, double* state, cudaStream_t s);
+void launch_p2p_fp64(Plan& P, const double* state, int B, double* u_s, int* err_flag, cudaStream_t s);
+
+}  // namespace demag
+
+// the opaque handle of the C ABI is the plan itself
+struct demag_plan_s : demag::Plan {};
