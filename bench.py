@@ -131,33 +131,52 @@ def measured_peaks():
 P2P_FLOPS_PER_PAIR = 470
 
 
-def roofline_for(stats, steps_profiled, precision, peaks):
-    """Roofline of the dominant stage from the live per-stage CUDA-event times."""
+def m2l_macs(p):
+    """Multiply-adds of one M2L pair for one state: #{(n, m): |n| + |m| <= p} = C(p+6, 6)."""
+    from math import comb
+
+    return comb(p + 6, 6)
+
+
+def alu_peak_tflops(kind, sm_mhz):
+    """Peak from unit counts x clock: 152 SMs x 128 FP32 lanes (FMA = 2 flops);
+    FP64 is 1/64 of that on GB300 (nominal 1.25 TFLOP/s at 2.07 GHz)."""
+    lanes = 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6
+    return lanes / 1e12 if kind == "fp32" else lanes / 64 / 1e12
+
+
+def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
+    """Roofline of the dominant stage from its live per-stage CUDA-event time."""
     ms = stats["stage_ms"]
     dom = max(ms, key=lambda k: ms[k])
-    per_launch_ms = ms[dom] / max(1, stats["stage_launches"][dom])
-    launches_per_eval = stats["stage_launches"][dom] / max(1, steps_profiled)
-    B = stats["_batch"]
-    out = {"kernel": dom, "stage_ms_per_step": {k: v / max(1, steps_profiled) for k, v in ms.items()}}
-    if dom == "p2p":
-        flops = stats["n_p2p_pairs"] * P2P_FLOPS_PER_PAIR * B / launches_per_eval
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        peak = peaks.get("fp64_tflops")
-        src = "measured" if peak else "fallback (nominal GB300 FP64 1.25 TFLOP/s)"
-        peak = peak or 1.25
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": src,
-                    "note": "FP64 pipe; transcendentals not counted in achieved"})
+    launches = max(1, stats["stage_launches"][dom])
+    per_launch_s = ms[dom] / launches * 1e-3
+    launches_per_eval = launches / max(1, steps_profiled)
+    B, p = stats["_batch"], stats["p"]
+    out = {"kernel": dom, "stage_ms_per_step": {k: round(v / max(1, steps_profiled), 4) for k, v in ms.items()},
+           "launches_per_step": launches_per_eval}
+    kind = "fp64" if precision == "fp64" else "fp32"
+    work = None
+    if dom == "m2l":
+        work = 2.0 * stats["n_m2l"] * m2l_macs(p) * B / launches_per_eval
+        note = f"algorithmic flops 2*C(p+6,6) per pair per state, {kind} CUDA cores"
+    elif dom == "p2p" and stats["near_mode"] == 0:
+        work = stats["n_p2p_pairs"] * P2P_FLOPS_PER_PAIR * B / launches_per_eval
+        kind = "fp64"
+        note = "FP64 pipe; transcendentals not counted"
+    elif dom == "p2p":
+        work = 2.0 * 3 * stats["n_near_cols"] * B / launches_per_eval
+        note = f"near-field application, 2 flops per stored coefficient per state, {kind}"
+    if work is not None:
+        achieved = work / per_launch_s / 1e12
+        peak = alu_peak_tflops(kind, sm_mhz)
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz or 2070:.0f} MHz"
+                                                     + (" / 64 (FP64)" if kind == "fp64" else ""),
+                    "note": note})
     else:
-        # other stages: report against HBM with the bytes they must move
-        nbytes = stats.get("_stage_bytes", {}).get(dom)
-        peak = peaks.get("hbm_gbs", 6800.0)
-        if nbytes:
-            achieved = nbytes / launches_per_eval / (per_launch_ms * 1e-3) / 1e9
-            out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None})
-        else:
-            out.update({"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None})
+        out.update({"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                    "frac": None, "traffic": None})
     return out
 
 
@@ -274,8 +293,33 @@ def run_ours(args, rank, world, local_rank):
         prof.eval(M, u, H)
     pst = prof.stats()
     pst["_batch"] = B
-    roof = roofline_for(pst, nprof, args.precision, measured_peaks())
+    pst["near_mode"] = args.near_mode
+    roof = roofline_for(pst, nprof, args.precision, measured_peaks(), clk.get("sm_mhz"))
     prof.close()
+
+    # FP64 GPU FMM of the same plan settings: throughput, and the accuracy gate
+    # of the metric (rel-L2 of u and H vs FP64, per state, max over states)
+    ref_info = None
+    if args.precision != "fp64" and not args.no_fp64_ref:
+        nref = min(B, 2)
+        p64 = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64",
+                   near_mode=1, max_batch=nref, device=dev)
+        u64, H64 = p64.eval(M[:nref])
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(2):
+            p64.eval(M[:1])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = ev0.elapsed_time(ev1) / 2
+        eu = max(float(torch.linalg.norm(u[k] - u64[k]) / torch.linalg.norm(u64[k])) for k in range(nref))
+        eh = max(float(torch.linalg.norm(H[k] - H64[k]) / torch.linalg.norm(H64[k])) for k in range(nref))
+        ref_info = {"fp64_gpu_fmm_evals_per_s": 1e3 / t64, "fp64_ms_per_eval": t64, "fp64_near_mode": 1,
+                    "rel_l2_u_vs_fp64": eu, "rel_l2_H_vs_fp64": eh, "states_checked": nref,
+                    "meets_1e-4": bool(eu <= 1e-4 and eh <= 1e-4),
+                    "speedup_vs_fp64_gpu_fmm": value / (1e3 / t64)}
+        p64.close()
 
     if rank != 0:
         return None
@@ -292,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
                    "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
                    "plan_ms": st0["plan_ms"]},
         "roofline": roof,
+        "fp64_reference": ref_info,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Mh.nbytes),
                 "d2h_bytes_per_step": int(B * nodes.shape[0] * 4 * 8)},
         "gpu_launches": int(launches),
@@ -339,9 +384,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere200k", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"])
-    ap.add_argument("--near-mode", type=int, default=0)
-    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16x3"])
+    ap.add_argument("--near-mode", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

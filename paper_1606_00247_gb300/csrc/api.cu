@@ -125,8 +125,11 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
     if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
     if (o.autotune != 0) fail(DEMAG_ERR_UNSUPPORTED, "autotune is reserved");
-    if (o.precision != DEMAG_FP64 || o.near_mode != 0)
-      fail(DEMAG_ERR_UNSUPPORTED, "only precision=DEMAG_FP64 with near_mode=0 is built in this version");
+    if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
+    if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X3)
+      fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
+    if (o.precision == DEMAG_MIXED_TF32 || o.precision == DEMAG_MIXED_BF16X3)
+      fail(DEMAG_ERR_UNSUPPORTED, "tensor-core M2L modes are not built in this version");
     P = new demag_plan_s();
     P->opt = o;
     P->p = o.p;
@@ -153,7 +156,10 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
   return guarded([&] {
     if (!plan || !M || !u) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
     if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
-    eval_fp64(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
+    if (plan->opt.precision == DEMAG_FP64)
+      eval_fp64(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
+    else
+      eval_mixed(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
   });
 }
 
@@ -179,7 +185,7 @@ demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
   o->n_m2l = plan->n_m2l;
   o->n_p2p = plan->n_p2p;
   o->n_p2p_pairs = plan->n_p2p_pairs;
-  o->n_near_cols = 0;
+  o->n_near_cols = plan->n_wentries / 3;
   o->device_bytes = plan->device_bytes;
   for (int a = 0; a < 3; a++) o->lo[a] = plan->lo[a];
   o->side = plan->side;

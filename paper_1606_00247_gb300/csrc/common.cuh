@@ -138,6 +138,26 @@ struct Plan {
   int64_t* nt_off = nullptr;        // nn + 1
   int32_t* nt_tet = nullptr;        // 4 nt, sorted tet ids
 
+  // host copies of the shapes (plan time)
+  std::vector<int4> h_range;
+  std::vector<int64_t> h_p2p_off;
+  std::vector<int32_t> h_p2p_src;
+
+  // precomputed near field (near_mode = 1), per P2P target leaf ti:
+  //   columns = unique source nodes of the tets of its P2P source leaves,
+  //   W[w_off[ti] + (col * n_T + i) * 3 + c] = sum over those tets t ni col of
+  //   int_t lambda_col(r') (r_i - r')_c / |r_i - r'|^3 dV'
+  int64_t n_wcols = 0, n_wentries = 0;
+  int64_t* w_coloff = nullptr;      // nT + 1
+  int32_t* w_cols = nullptr;        // sorted node ids
+  int64_t* w_off = nullptr;         // nT + 1, in units of doubles
+  double* W64 = nullptr;
+  float* W32 = nullptr;
+
+  // FP32 far-field operators (mixed precision, per-level scaled)
+  float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)
+  float* cell_side32 = nullptr;     // per cell side length (float)
+
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
   Workspace* ws = nullptr;
@@ -187,6 +207,33 @@ void dfree_all(Plan& P);
 void build_plan(Plan& P, const double* nodes, const int32_t* tets);
 void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 void destroy_workspace(Plan& P);
+
+// evaluation workspace (one per plan, sized for max_batch states)
+struct Workspace {
+  int B = 0;
+  double *Ms = nullptr, *Q = nullptr, *L = nullptr, *u_s = nullptr, *state = nullptr;
+  float *Ms32 = nullptr, *Q32 = nullptr, *L32 = nullptr, *u32 = nullptr;
+  double *M_dev = nullptr, *u_dev = nullptr, *H_dev = nullptr;  // staging for host pointers
+  int* err = nullptr;
+  std::vector<void*> ptrs;
+};
+Workspace& workspace(Plan& P, int B);
+bool is_device_ptr(const void* p);
+// shared FP64 stages (fmm.cu)
+bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, const double** Md, double** ud,
+                   double** Hd, cudaStream_t s);
+void eval_io_end(Plan& P, Workspace& W, bool dev, int B, double* u, double* H, cudaStream_t s);
+void near_field_fp64(Plan& P, Workspace& W, int B, StageClock& clk, cudaStream_t s);
+void launch_gather_M(Plan& P, const double* M, int B, double* Ms, cudaStream_t s);
+void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H, cudaStream_t s);
+
+// precomputed near field (near.cu)
+void build_near_field(Plan& P);
+void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s);
+void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, cudaStream_t s);
+// mixed-precision far field (fmm32.cu)
+void build_mixed_operators(Plan& P);
+void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);

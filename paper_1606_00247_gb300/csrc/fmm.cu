@@ -135,10 +135,11 @@ __global__ void k_m2l_fp64(const int32_t* __restrict__ targets, const int64_t* _
   load_mi(nc, mi);
   const int32_t T = targets[blockIdx.x];
   const double cx = centre[3 * T], cy = centre[3 * T + 1], cz = centre[3 * T + 2];
-  constexpr int PER = (MAX_NCOEF + 127) / 128;  // (m,b) items per thread when B == 1 and blockDim == 128
+  // this block handles the (m, state) items [i0, i1): at most PER per thread
+  constexpr int PER = 4;
+  const int i0 = blockIdx.y * blockDim.x * PER, i1 = min(nc * B, i0 + (int)blockDim.x * PER);
   double acc[PER];
   for (int r = 0; r < PER; r++) acc[r] = 0;
-  // items beyond PER*blockDim are handled by the generic path below
   for (int64_t e = m2l_off[T]; e < m2l_off[T + 1]; e++) {
     const int32_t S = m2l_src[e];
     const double x = cx - centre[3 * S], y = cy - centre[3 * S + 1], z = cz - centre[3 * S + 2];
@@ -164,7 +165,7 @@ __global__ void k_m2l_fp64(const int32_t* __restrict__ targets, const int64_t* _
     }
     const double* Qs = Q + (int64_t)S * nc * B;
     int r = 0;
-    for (int idx = threadIdx.x; idx < nc * B; idx += blockDim.x, r++) {
+    for (int idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x, r++) {
       const int m = idx / B, b = idx - m * B;
       const int ma = mi[m][0], mb = mi[m][1], mz = mi[m][2];
       const int tm = ma + mb + mz;
@@ -177,23 +178,16 @@ __global__ void k_m2l_fp64(const int32_t* __restrict__ targets, const int64_t* _
             const int na = t - j, nz = cz2, nb = j - cz2;
             a += bk[mi_index(na + ma, nb + mb, nz + mz)] * Qs[(int64_t)n * B + b];
           }
-      if (r < PER)
-        acc[r] += a;
-      else
-        L[((int64_t)T * nc + m) * B + b] += a;  // rare: more items than registers
+      acc[r] += a;
     }
   }
   int r = 0;
   const double inv4pi = 1.0 / (4.0 * M_PI);
-  for (int idx = threadIdx.x; idx < nc * B; idx += blockDim.x, r++) {
+  for (int idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x, r++) {
     const int m = idx / B, b = idx - m * B;
     const int tm = mi[m][0] + mi[m][1] + mi[m][2];
     const double sg = (tm & 1) ? -inv4pi : inv4pi;
-    double* dst = L + ((int64_t)T * nc + m) * B + b;
-    if (r < PER)
-      *dst = sg * acc[r];
-    else
-      *dst *= sg;
+    L[((int64_t)T * nc + m) * B + b] = sg * acc[r];
   }
 }
 
@@ -295,15 +289,6 @@ __global__ void k_lumped_H_out(int64_t nn, int B, const int32_t* __restrict__ pe
 // ---------------------------------------------------------------------------
 // workspace and the FP64 driver
 // ---------------------------------------------------------------------------
-struct Workspace {
-  int B = 0;
-  bool host_io = false;
-  double *Ms = nullptr, *Q = nullptr, *L = nullptr, *u_s = nullptr, *state = nullptr;
-  double *M_dev = nullptr, *u_dev = nullptr, *H_dev = nullptr;  // staging for host pointers
-  int* err = nullptr;
-  std::vector<void*> ptrs;
-};
-
 static void* ws_alloc(Workspace& W, size_t bytes) {
   void* p = nullptr;
   if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
@@ -321,18 +306,26 @@ void destroy_workspace(Plan& P) {
   P.ws = nullptr;
 }
 
-static Workspace& workspace(Plan& P, int B) {
+Workspace& workspace(Plan& P, int B) {
   int need = std::max(B, P.opt.max_batch);
   if (P.ws && P.ws->B >= need) return *P.ws;
   destroy_workspace(P);
   Workspace* W = new Workspace();
   W->B = need;
   const size_t nn = P.nn, nt = P.nt, nc = P.nc, ncell = P.ncells;
+  const bool mixed = P.opt.precision != DEMAG_FP64, otf = P.opt.near_mode == 0;
   W->Ms = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
-  W->Q = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
-  W->L = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
+  if (!mixed) {
+    W->Q = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
+    W->L = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
+  } else {
+    W->Ms32 = (float*)ws_alloc(*W, sizeof(float) * nn * 3 * need);
+    W->Q32 = (float*)ws_alloc(*W, sizeof(float) * ncell * nc * need);
+    W->L32 = (float*)ws_alloc(*W, sizeof(float) * ncell * nc * need);
+    W->u32 = (float*)ws_alloc(*W, sizeof(float) * nn * need);
+  }
   W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);
-  W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);
+  if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);
   W->M_dev = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
   W->u_dev = (double*)ws_alloc(*W, sizeof(double) * nn * need);
   W->H_dev = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
@@ -341,7 +334,7 @@ static Workspace& workspace(Plan& P, int B) {
   return *W;
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -352,20 +345,11 @@ static bool is_device_ptr(const void* p) {
 
 void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s) {
   Workspace& W = workspace(P, B);
-  const bool dev = is_device_ptr(M);
-  if (dev != is_device_ptr(u) || (H && dev != is_device_ptr(H)))
-    fail(DEMAG_ERR_INVALID_ARG, "M, u and H must be all device or all host pointers");
-  const double* Md = M;
-  double *ud = u, *Hd = H;
-  if (!dev) {
-    DM_CUDA(cudaMemcpyAsync(W.M_dev, M, sizeof(double) * P.nn * 3 * B, cudaMemcpyHostToDevice, s));
-    Md = W.M_dev;
-    ud = W.u_dev;
-    Hd = H ? W.H_dev : nullptr;
-  }
+  const double* Md;
+  double *ud, *Hd;
+  const bool dev = eval_io_begin(P, W, M, B, u, H, &Md, &ud, &Hd, s);
   const int p = P.p, nc = P.nc;
   StageClock clk(P, s);
-  DM_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), s));
   clk.begin(DEMAG_STAGE_GATHER);
   k_gather_M<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms);
   DM_LAUNCH("k_gather_M");
@@ -393,8 +377,8 @@ void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream
   clk.begin(DEMAG_STAGE_M2L);
   DM_CUDA(cudaMemsetAsync(W.L, 0, sizeof(double) * P.ncells * nc * B, s));
   if (!P.h_m2l_targets.empty()) {
-    k_m2l_fp64<<<(unsigned)P.h_m2l_targets.size(), 128, 0, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre,
-                                                                 p, nc, B, W.Q, W.L);
+    dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((nc * B + 128 * 4 - 1) / (128 * 4)));
+    k_m2l_fp64<<<grid, 128, 0, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre, p, nc, B, W.Q, W.L);
     DM_LAUNCH("k_m2l_fp64");
     clk.launched();
   }
@@ -414,6 +398,26 @@ void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream
   clk.launched();
   clk.end();
   // near field
+  near_field_fp64(P, W, B, clk, s);
+  // lumped H and output layout
+  clk.begin(DEMAG_STAGE_H);
+  launch_lumped_H_out(P, B, W.u_s, ud, Hd, s);
+  clk.launched();
+  clk.end();
+  clk.finish();
+  eval_io_end(P, W, dev, B, u, H, s);
+}
+
+void near_field_fp64(Plan& P, Workspace& W, int B, StageClock& clk, cudaStream_t s) {
+  if (P.opt.near_mode == 1) {
+    clk.begin(DEMAG_STAGE_P2P);
+    if (!P.h_p2p_targets.empty()) {
+      launch_near_apply64(P, W.Ms, B, W.u_s, s);
+      clk.launched();
+    }
+    clk.end();
+    return;
+  }
   clk.begin(DEMAG_STAGE_NEAR_PREP);
   launch_tet_state(P, W.Ms, B, W.state, s);
   clk.launched();
@@ -424,22 +428,46 @@ void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream
     clk.launched();
   }
   clk.end();
-  // lumped H and output layout
-  clk.begin(DEMAG_STAGE_H);
+}
+
+void launch_gather_M(Plan& P, const double* M, int B, double* Ms, cudaStream_t s) {
+  k_gather_M<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, M, Ms);
+  DM_LAUNCH("k_gather_M");
+}
+
+void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H, cudaStream_t s) {
   k_lumped_H_out<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, P.nt_off, P.nt_tet, P.tets_s, P.tet_grad,
-                                                 P.tet_vol, W.u_s, ud, Hd);
+                                                 P.tet_vol, u_s, u, H);
   DM_LAUNCH("k_lumped_H_out");
-  clk.launched();
-  clk.end();
-  clk.finish();
+}
+
+// host/device pointer handling shared by the drivers
+bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, const double** Md, double** ud,
+                   double** Hd, cudaStream_t s) {
+  const bool dev = is_device_ptr(M);
+  if (dev != is_device_ptr(u) || (H && dev != is_device_ptr(H)))
+    fail(DEMAG_ERR_INVALID_ARG, "M, u and H must be all device or all host pointers");
+  *Md = M;
+  *ud = u;
+  *Hd = H;
   if (!dev) {
-    DM_CUDA(cudaMemcpyAsync(u, W.u_dev, sizeof(double) * P.nn * B, cudaMemcpyDeviceToHost, s));
-    if (H) DM_CUDA(cudaMemcpyAsync(H, W.H_dev, sizeof(double) * P.nn * 3 * B, cudaMemcpyDeviceToHost, s));
-    int herr = 0;
-    DM_CUDA(cudaMemcpyAsync(&herr, W.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    DM_CUDA(cudaStreamSynchronize(s));
-    if (herr) fail((demag_status)herr, "a bounded device wait expired in the near-field kernel");
+    DM_CUDA(cudaMemcpyAsync(W.M_dev, M, sizeof(double) * P.nn * 3 * B, cudaMemcpyHostToDevice, s));
+    *Md = W.M_dev;
+    *ud = W.u_dev;
+    *Hd = H ? W.H_dev : nullptr;
   }
+  DM_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), s));
+  return dev;
+}
+
+void eval_io_end(Plan& P, Workspace& W, bool dev, int B, double* u, double* H, cudaStream_t s) {
+  if (dev) return;
+  DM_CUDA(cudaMemcpyAsync(u, W.u_dev, sizeof(double) * P.nn * B, cudaMemcpyDeviceToHost, s));
+  if (H) DM_CUDA(cudaMemcpyAsync(H, W.H_dev, sizeof(double) * P.nn * 3 * B, cudaMemcpyDeviceToHost, s));
+  int herr = 0;
+  DM_CUDA(cudaMemcpyAsync(&herr, W.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  if (herr) fail((demag_status)herr, "a bounded device wait expired in the near-field kernel");
 }
 
 }  // namespace demag

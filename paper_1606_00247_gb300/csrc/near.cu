@@ -1,0 +1,264 @@
+// near.cu -- precomputed near field (near_mode = 1).
+//
+// Sec. 3.4 of the paper stores the direct-interaction coefficients instead of
+// recomputing them.  Here, per P2P target leaf T, the columns are the unique
+// nodes j of the tets of T's P2P source leaves, and
+//     W[j][i][c] = 1/(4 pi) sum_{t in near(T), t ni j} int_t lambda_j(r') (r_i - r')_c / |r_i - r'|^3 dV'
+// for every node i of T, so that u_near(r_i) = sum_j W[j][i] . M_j.  The
+// integrals are the FP64 analytic pair integrals of p2p.cuh (W-form:
+// W_k = lambda_k(r) a + T g_k / 2), computed once at plan time.  At every
+// evaluation the near field is then a block-sparse product with the nodal M
+// of all B states (FP64 for the FP64 path, FP32 for the mixed paths).
+#include <cub/cub.cuh>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "p2p.cuh"
+
+namespace demag {
+
+namespace {
+
+template <class T>
+struct Tmp {
+  T* p = nullptr;
+  explicit Tmp(size_t n) {
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      fail(DEMAG_ERR_OUT_OF_MEMORY, "near-field temporary allocation failed");
+    }
+  }
+  ~Tmp() {
+    if (p) cudaFree(p);
+  }
+};
+
+__global__ void k_near_keys(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                            const int64_t* __restrict__ p2p_off, const int32_t* __restrict__ p2p_src,
+                            const int32_t* __restrict__ tets_s, const int64_t* __restrict__ key_off, uint64_t* keys) {
+  const int64_t ti = blockIdx.x;
+  const int32_t T = targets[ti];
+  int64_t o = key_off[ti];
+  for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
+    const int4 r = range[p2p_src[e]];
+    const int64_t n = 4ll * (r.y - r.x);
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
+      keys[o + q] = ((uint64_t)ti << 32) | (uint32_t)tets_s[4ll * r.x + q];
+    o += n;
+  }
+}
+
+__global__ void k_col_offsets(const uint64_t* __restrict__ keys, int64_t n, int64_t nT, int64_t* off, int32_t* cols) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c <= nT) {
+    uint64_t k = (uint64_t)c << 32;
+    int64_t b = 0, e = n;
+    while (b < e) {
+      int64_t m = (b + e) >> 1;
+      if (keys[m] < k)
+        b = m + 1;
+      else
+        e = m;
+    }
+    off[c] = b;
+  }
+  if (c < n) cols[c] = (int32_t)(keys[c] & 0xffffffffu);
+}
+
+constexpr int NB_CHUNK = 32;
+constexpr int NB_COLCACHE = 4096;
+
+// one block per P2P target leaf; (target node, source tet) pairs over threads
+__global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                                                    const int64_t* __restrict__ p2p_off,
+                                                    const int32_t* __restrict__ p2p_src,
+                                                    const double* __restrict__ nodes_s,
+                                                    const int32_t* __restrict__ tets_s,
+                                                    const double* __restrict__ geo, const double* __restrict__ grad,
+                                                    const int64_t* __restrict__ coloff,
+                                                    const int32_t* __restrict__ cols, const int64_t* __restrict__ woff,
+                                                    double* W) {
+  __shared__ double s_geo[NB_CHUNK * TET_GEO];
+  __shared__ double s_grad[NB_CHUNK * 12];
+  __shared__ int32_t s_node[NB_CHUNK * 4];
+  __shared__ int32_t s_cols[NB_COLCACHE];
+  const int64_t ti = blockIdx.x;
+  const int32_t T = targets[ti];
+  const int4 rT = range[T];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
+  const bool cached = ncol <= NB_COLCACHE;
+  if (cached)
+    for (int64_t q = threadIdx.x; q < ncol; q += blockDim.x) s_cols[q] = cols[c0 + q];
+  const int32_t* colv = cached ? s_cols : cols + c0;
+  double* Wt = W + woff[ti];
+  const double inv4pi = 1.0 / (4.0 * M_PI);
+  for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
+    const int4 rS = range[p2p_src[e]];
+    for (int32_t j0 = rS.x; j0 < rS.y; j0 += NB_CHUNK) {
+      const int ns = min(NB_CHUNK, rS.y - j0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < ns * TET_GEO; q += blockDim.x) s_geo[q] = geo[(int64_t)j0 * TET_GEO + q];
+      for (int q = threadIdx.x; q < ns * 12; q += blockDim.x) s_grad[q] = grad[(int64_t)j0 * 12 + q];
+      for (int q = threadIdx.x; q < ns * 4; q += blockDim.x) s_node[q] = tets_s[4ll * j0 + q];
+      __syncthreads();
+      for (int q = threadIdx.x; q < nT * ns; q += blockDim.x) {
+        const int i = q / ns, t = q - i * ns;
+        const double* r = nodes_s + 3ll * (rT.z + i);
+        const double* G = s_geo + t * TET_GEO;
+        PairAT at;
+        pair_at(G, r[0], r[1], r[2], at);
+        const double* g = s_grad + 12 * t;
+        const double d0 = r[0] - G[0], d1 = r[1] - G[1], d2 = r[2] - G[2];
+        double lam[4];
+        lam[1] = g[3] * d0 + g[4] * d1 + g[5] * d2;
+        lam[2] = g[6] * d0 + g[7] * d1 + g[8] * d2;
+        lam[3] = g[9] * d0 + g[10] * d1 + g[11] * d2;
+        lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+        for (int k = 0; k < 4; k++) {
+          const double gx = g[3 * k], gy = g[3 * k + 1], gz = g[3 * k + 2];
+          const double w0 = lam[k] * at.a[0] + 0.5 * (at.T[0] * gx + at.T[3] * gy + at.T[4] * gz);
+          const double w1 = lam[k] * at.a[1] + 0.5 * (at.T[3] * gx + at.T[1] * gy + at.T[5] * gz);
+          const double w2 = lam[k] * at.a[2] + 0.5 * (at.T[4] * gx + at.T[5] * gy + at.T[2] * gz);
+          // column of the vertex: binary search in the sorted column list
+          const int32_t node = s_node[4 * t + k];
+          int64_t lo = 0, hi = ncol;
+          while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (colv[mid] < node)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          double* dst = Wt + (lo * nT + i) * 3;
+          atomicAdd(dst, w0 * inv4pi);
+          atomicAdd(dst + 1, w1 * inv4pi);
+          atomicAdd(dst + 2, w2 * inv4pi);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// u_s[i][b] += sum_col W[col][i] . M[node(col)][.][b]; one block per target leaf
+template <class T>
+__global__ void k_near_apply(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                             const int64_t* __restrict__ coloff, const int32_t* __restrict__ cols,
+                             const int64_t* __restrict__ woff, const T* __restrict__ W, const T* __restrict__ Ms, int B,
+                             T* u_s) {
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], c1 = coloff[ti + 1];
+  const T* Wt = W + woff[ti];
+  for (int item = threadIdx.x; item < nT * B; item += blockDim.x) {
+    const int i = item / B, b = item - i * B;
+    T acc = 0;
+    for (int64_t c = c0; c < c1; c++) {
+      const T* w = Wt + ((c - c0) * nT + i) * 3;
+      const T* m = Ms + (int64_t)cols[c] * 3 * B + b;
+      acc += w[0] * m[0] + w[1] * m[B] + w[2] * m[2 * B];
+    }
+    u_s[(int64_t)(rT.z + i) * B + b] += acc;
+  }
+}
+
+}  // namespace
+
+void build_near_field(Plan& P) {
+  cudaStream_t s = P.stream;
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
+  P.w_coloff = dalloc<int64_t>(P, nT + 1);
+  P.w_off = dalloc<int64_t>(P, nT + 1);
+  if (nT == 0) {
+    DM_CUDA(cudaMemsetAsync(P.w_coloff, 0, sizeof(int64_t), s));
+    DM_CUDA(cudaMemsetAsync(P.w_off, 0, sizeof(int64_t), s));
+    P.w_cols = dalloc<int32_t>(P, 1);
+    P.W64 = dalloc<double>(P, 1);
+    if (P.opt.precision != DEMAG_FP64) P.W32 = dalloc<float>(P, 1);
+    return;
+  }
+  std::vector<int64_t> koff(nT + 1, 0);
+  for (int64_t ti = 0; ti < nT; ti++) {
+    int32_t T = P.h_p2p_targets[ti];
+    int64_t n = 0;
+    for (int64_t e = P.h_p2p_off[T]; e < P.h_p2p_off[T + 1]; e++) {
+      int4 r = P.h_range[P.h_p2p_src[e]];
+      n += 4ll * (r.y - r.x);
+    }
+    koff[ti + 1] = koff[ti] + n;
+  }
+  const int64_t nk = koff[nT];
+  if (nk > (int64_t)INT32_MAX) fail(DEMAG_ERR_UNSUPPORTED, "near field too large for the precomputed mode");
+  Tmp<int64_t> dkoff(nT + 1);
+  DM_CUDA(cudaMemcpyAsync(dkoff.p, koff.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  int64_t ncols = 0;
+  {
+    Tmp<uint64_t> keys(nk), keys_s(nk);
+    k_near_keys<<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.tets_s, dkoff.p,
+                                              keys.p);
+    DM_LAUNCH("k_near_keys");
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, tb, keys.p, keys_s.p, (int)nk, 0, 64, s);
+    Tmp<char> temp(tb);
+    DM_CUDA(cub::DeviceRadixSort::SortKeys(temp.p, tb, keys.p, keys_s.p, (int)nk, 0, 64, s));
+    Tmp<int> nu(1);
+    size_t tb2 = 0;
+    cub::DeviceSelect::Unique(nullptr, tb2, keys_s.p, keys.p, nu.p, (int)nk, s);
+    Tmp<char> temp2(tb2);
+    DM_CUDA(cub::DeviceSelect::Unique(temp2.p, tb2, keys_s.p, keys.p, nu.p, (int)nk, s));
+    int hnu = 0;
+    DM_CUDA(cudaMemcpyAsync(&hnu, nu.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    ncols = hnu;
+    P.w_cols = dalloc<int32_t>(P, std::max<int64_t>(ncols, 1));
+    k_col_offsets<<<(unsigned)((std::max<int64_t>(ncols, nT + 1) + 255) / 256), 256, 0, s>>>(keys.p, ncols, nT,
+                                                                                          P.w_coloff, P.w_cols);
+    DM_LAUNCH("k_col_offsets");
+  }
+  std::vector<int64_t> hcol(nT + 1), hw(nT + 1, 0);
+  DM_CUDA(cudaMemcpyAsync(hcol.data(), P.w_coloff, (nT + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  for (int64_t ti = 0; ti < nT; ti++) {
+    int4 r = P.h_range[P.h_p2p_targets[ti]];
+    hw[ti + 1] = hw[ti] + (hcol[ti + 1] - hcol[ti]) * (int64_t)(r.w - r.z) * 3;
+  }
+  P.n_wcols = ncols;
+  P.n_wentries = hw[nT];
+  DM_CUDA(cudaMemcpyAsync(P.w_off, hw.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  P.W64 = dalloc<double>(P, std::max<int64_t>(P.n_wentries, 1));
+  DM_CUDA(cudaMemsetAsync(P.W64, 0, std::max<int64_t>(P.n_wentries, 1) * sizeof(double), s));
+  k_near_build<<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s, P.tets_s,
+                                            P.tet_geo, P.tet_grad, P.w_coloff, P.w_cols, P.w_off, P.W64);
+  DM_LAUNCH("k_near_build");
+  if (P.opt.precision != DEMAG_FP64) {
+    P.W32 = dalloc<float>(P, std::max<int64_t>(P.n_wentries, 1));
+    k_f64_to_f32<<<1024, 256, 0, s>>>(P.W64, P.W32, P.n_wentries);
+    DM_LAUNCH("k_f64_to_f32");
+  }
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
+void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s) {
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
+  if (!nT) return;
+  k_near_apply<double><<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off, P.W64,
+                                                    Ms, B, u_s);
+  DM_LAUNCH("k_near_apply<double>");
+}
+
+void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, cudaStream_t s) {
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
+  if (!nT) return;
+  k_near_apply<float><<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off, P.W32,
+                                                   Ms, B, u_s);
+  DM_LAUNCH("k_near_apply<float>");
+}
+
+}  // namespace demag

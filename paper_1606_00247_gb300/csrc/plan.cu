@@ -934,6 +934,11 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     DM_CUDA(cudaStreamSynchronize(s));
   }
 
+  P.h_range = std::move(h_range);
+  P.h_p2p_off = std::move(h_p2p_off);
+  P.h_p2p_src = std::move(h_p2p_src);
+  if (P.opt.near_mode == 1) build_near_field(P);
+  if (P.opt.precision != DEMAG_FP64) build_mixed_operators(P);
   DM_CUDA(cudaStreamSynchronize(s));
   P.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -1,0 +1,117 @@
+"""Precomputed near field (near_mode=1) and the mixed-precision path.
+
+* near_mode=1 in FP64 computes the same sums as near_mode=0 (coefficients
+  integrated once, applied per state), so the two agree to rounding, and
+  both agree with the oracle FMM.
+* The mixed path (FP32 expansions scaled per level, FP32 application of the
+  FP64 near-field coefficients) is held to the stated bar: rel-L2 <= 1e-4 of u
+  and of H against the FP64 path of the same plan at p = 8, per state.  FP32
+  rounding of O(1)-scaled coefficients gives ~1e-6 in practice, asserted too.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1606_00247_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def per_state(a, b):
+    return max(rel_l2(a[k], b[k]) for k in range(a.shape[0]))
+
+
+def _plan(nodes, tets, **kw):
+    from paper_1606_00247_gb300.api import Plan
+
+    return Plan(nodes, tets, **kw)
+
+
+def test_near_mode1_fp64_equals_on_the_fly(orc):
+    nodes, tets = inputs.sphere(h=0.14)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=3)
+    u0, H0 = _plan(nodes, tets, p=5, leaf_size=16, max_batch=3, near_mode=0).eval(M)
+    u1, H1 = _plan(nodes, tets, p=5, leaf_size=16, max_batch=3, near_mode=1).eval(M)
+    assert rel_l2(u1.cpu(), u0.cpu()) < 1e-12 and rel_l2(H1.cpu(), H0.cpu()) < 1e-12
+    ref = orc.Tree(nodes, tets, 16, 0.5).fmm(M, 5)
+    assert rel_l2(u1.cpu().numpy(), ref) < 1e-10
+
+
+def test_near_mode1_theta_zero_is_direct(orc):
+    nodes, tets = inputs.unit_cube(4)
+    M = inputs.gaussian_unit_m(nodes.shape[0])
+    u, _ = _plan(nodes, tets, p=2, leaf_size=8, theta=1e-9, near_mode=1).eval(M)
+    assert rel_l2(u.cpu().numpy(), orc.direct(nodes, tets, M)) < 1e-12
+
+
+@pytest.mark.parametrize("near_mode", [0, 1])
+@pytest.mark.parametrize("p", [4, 8])
+def test_mixed_vs_fp64(orc, near_mode, p):
+    nodes, tets = inputs.sphere(h=0.1)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=4)
+    u64, H64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=4, near_mode=1).eval(M)
+    u32, H32 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=4, near_mode=near_mode, precision="fp32").eval(M)
+    eu = per_state(u32.cpu().numpy(), u64.cpu().numpy())
+    eh = per_state(H32.cpu().numpy(), H64.cpu().numpy())
+    assert eu <= 1e-4 and eh <= 1e-4
+    assert eu < 2e-6 and eh < 2e-5, (eu, eh)
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1e3])
+def test_mixed_scale_invariance(orc, scale):
+    """Per-level scaling keeps FP32 in range for any mesh size."""
+    nodes, tets = inputs.sphere(h=0.15)
+    nodes = nodes * scale
+    M = inputs.gaussian_unit_m(nodes.shape[0])
+    u64, H64 = _plan(nodes, tets, p=8, leaf_size=16, near_mode=1).eval(M)
+    u32, H32 = _plan(nodes, tets, p=8, leaf_size=16, near_mode=1, precision="fp32").eval(M)
+    assert rel_l2(u32.cpu(), u64.cpu()) < 2e-6 and rel_l2(H32.cpu(), H64.cpu()) < 2e-5
+    # u scales like length (M.r), H is scale free
+    u1, H1 = _plan(nodes / scale, tets, p=8, leaf_size=16, near_mode=1).eval(M)
+    assert rel_l2(u64.cpu() / scale, u1.cpu()) < 1e-9 and rel_l2(H64.cpu(), H1.cpu()) < 1e-9
+
+
+def test_mixed_batch_equals_singles():
+    nodes, tets = inputs.sphere(h=0.2)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=5)
+    plan = _plan(nodes, tets, p=6, leaf_size=16, max_batch=5, near_mode=1, precision="fp32")
+    ub, Hb = plan.eval(M)
+    for b in range(5):
+        u1, H1 = plan.eval(M[b])
+        assert rel_l2(u1.cpu(), ub[b].cpu()) < 1e-6 and rel_l2(H1.cpu(), Hb[b].cpu()) < 1e-6
+
+
+def test_mixed_host_pointers():
+    nodes, tets = inputs.unit_cube(6)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=2)
+    plan = _plan(nodes, tets, p=6, leaf_size=16, max_batch=2, near_mode=1, precision="fp32")
+    ud, Hd = plan.eval(M)
+    uh, Hh = plan.eval_host(M)
+    assert np.array_equal(uh, ud.cpu().numpy()) and np.array_equal(Hh, Hd.cpu().numpy())
+
+
+def test_bench_workload_mixed_vs_fp64_and_oracle_sample(orc):
+    """The configuration bench.py times (ball of ~220k tets, p=8, theta=0.5,
+    leaf 32, batch of states): mixed vs FP64 on every node, and FP64 vs the
+    oracle FMM on sampled target leaves computed one by one."""
+    nodes, tets = inputs.sphere(h=inputs.SPHERE_200K_H)
+    B = 4
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=B)
+    p64 = _plan(nodes, tets, p=8, leaf_size=32, theta=0.5, max_batch=B, near_mode=1)
+    u64, H64 = p64.eval(M)
+    p32 = _plan(nodes, tets, p=8, leaf_size=32, theta=0.5, max_batch=B, near_mode=1, precision="fp32")
+    u32, H32 = p32.eval(M)
+    assert per_state(u32.cpu().numpy(), u64.cpu().numpy()) <= 1e-4
+    assert per_state(H32.cpu().numpy(), H64.cpu().numpy()) <= 1e-4
+    tr = orc.Tree(nodes, tets, 32, 0.5)
+    ex = tr.export()
+    leaves = np.where((ex["cell_child"][:, 1] == 0) & (ex["cell_ranges"][:, 3] > ex["cell_ranges"][:, 2]))[0]
+    pick = leaves[np.linspace(0, len(leaves) - 1, 40).astype(int)]
+    ref = tr.fmm(M[0], 8, target_leaves=pick)
+    sel = np.concatenate([ex["node_perm"][ex["cell_ranges"][c, 2]:ex["cell_ranges"][c, 3]] for c in pick])
+    assert rel_l2(u64[0].cpu().numpy()[sel], ref[sel]) < 1e-10
