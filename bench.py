@@ -40,6 +40,31 @@ WORKLOADS = {
 }
 
 
+def aggregate_ranks(total_ms, evals_per_rank, world, device):
+    """Whole-job throughput of replicas: every rank evaluated `evals_per_rank`
+    (mesh, state) pairs in `total_ms`; the job time is the maximum over ranks
+    and the value is all ranks' evaluations over that time.  Returns
+    (max_ms, evals/s).  With world > 1 the process group must be initialised."""
+    if world > 1:
+        import torch
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    return total_ms, world * evals_per_rank / (total_ms * 1e-3)
+
+
+def workload(args):
+    """The named workload with any --p / --leaf / --theta overrides."""
+    w = dict(WORKLOADS[args.workload])
+    for k in ("p", "leaf", "theta"):
+        v = getattr(args, k, None)
+        if v:
+            w[k] = v
+    return w
+
+
 def make_mesh(w):
     from paper_1606_00247_gb300 import inputs
 
@@ -230,9 +255,7 @@ def run_ours(args, rank, world, local_rank):
     build()
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
-    w = dict(WORKLOADS[args.workload])
-    if args.p:
-        w["p"] = args.p
+    w = workload(args)
     nodes, tets = make_mesh(w)
     B = args.batch
     plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
@@ -264,12 +287,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     launches = plan.stats()["eval_launches"] * args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
-    value = world * B * args.steps / (total_ms * 1e-3)
+    total_ms, value = aggregate_ranks(total_ms, B * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside)
     Mh = make_M(nodes.shape[0], B, seed_offset=rank)
@@ -351,9 +369,7 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    w = dict(WORKLOADS[args.workload])
-    if args.p:
-        w["p"] = args.p
+    w = workload(args)
     nodes, tets = make_mesh(w)
     M1 = make_M(nodes.shape[0], 1)[0]
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
@@ -389,6 +405,8 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--leaf", type=int, default=0)
+    ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -152,6 +152,7 @@ struct Plan {
   int32_t* w_cols = nullptr;        // sorted node ids
   int64_t* w_off = nullptr;         // nT + 1, in units of doubles
   double* W64 = nullptr;
+  int64_t* w_off32 = nullptr;       // nT + 1, in floats; W32 is [col][node][4]
   float* W32 = nullptr;
 
   // FP32 far-field operators (mixed precision, per-level scaled)
@@ -230,10 +231,11 @@ void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H
 // precomputed near field (near.cu)
 void build_near_field(Plan& P);
 void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s);
-void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, cudaStream_t s);
+void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s);
 // mixed-precision far field (fmm32.cu)
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
+bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, cudaStream_t s);  // m2l32.cu
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);

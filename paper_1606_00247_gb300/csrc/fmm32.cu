@@ -303,7 +303,10 @@ void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStrea
   clk.end();
   clk.begin(DEMAG_STAGE_M2L);
   DM_CUDA(cudaMemsetAsync(W.L32, 0, sizeof(float) * P.ncells * nc * B, s));
-  if (!P.h_m2l_targets.empty()) {
+  if (P.h_m2l_targets.empty()) {
+  } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, s)) {
+    clk.launched();
+  } else {
     dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((nc * B + 128 * 8 - 1) / (128 * 8)));
     k_m2l32<<<grid, 128, 0, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre, P.cell_level, P.side, p, nc, B,
                                  W.Q32, W.L32);
@@ -332,7 +335,7 @@ void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStrea
   } else {
     clk.begin(DEMAG_STAGE_P2P);
     if (!P.h_p2p_targets.empty()) {
-      launch_near_apply32(P, W.Ms32, B, W.u32, s);
+      launch_near_apply32(P, W.Ms32, B, W.u32, W.err, s);
       clk.launched();
     }
     clk.end();

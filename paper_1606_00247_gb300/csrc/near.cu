@@ -141,10 +141,6 @@ __global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ 
   }
 }
 
-__global__ void k_f64_to_f32(const double* __restrict__ a, float* b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
 
 // u_s[i][b] += sum_col W[col][i] . M[node(col)][.][b]; one block per target leaf
 template <class T>
@@ -166,6 +162,145 @@ __global__ void k_near_apply(const int32_t* __restrict__ targets, const int4* __
       acc += w[0] * m[0] + w[1] * m[B] + w[2] * m[2 * B];
     }
     u_s[(int64_t)(rT.z + i) * B + b] += acc;
+  }
+}
+
+// FP32 copy in the layout of the mixed apply: [col][target node][4] (x, y, z, 0)
+__global__ void k_pack_w32(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                           const int64_t* __restrict__ coloff, const int64_t* __restrict__ woff,
+                           const int64_t* __restrict__ woff32, const double* __restrict__ W, float* W32) {
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int64_t nT = rT.w - rT.z, n = (coloff[ti + 1] - coloff[ti]) * nT;
+  const double* src = W + woff[ti];
+  float4* dst = (float4*)(W32 + woff32[ti]);
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
+    dst[q] = make_float4((float)src[3 * q], (float)src[3 * q + 1], (float)src[3 * q + 2], 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy + mbarrier helpers (sm_90+ PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (long it = 0; it < (1l << 24); it++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+constexpr int NA_COLS = 32;  // columns per staged chunk
+constexpr int NA_NT = 32;    // target nodes per pass (registers)
+
+// u[i][b] += sum_col W[col][i] . M[node(col)][.][b]
+// block per (target leaf, 128-state slice); thread = state; all target nodes of
+// the pass in registers; W chunks double-buffered in shared memory by TMA.
+__global__ void __launch_bounds__(128) k_near_apply32(const int32_t* __restrict__ targets,
+                                                      const int4* __restrict__ range,
+                                                      const int64_t* __restrict__ coloff,
+                                                      const int32_t* __restrict__ cols,
+                                                      const int64_t* __restrict__ woff32,
+                                                      const float* __restrict__ W32, const float* __restrict__ Ms,
+                                                      int B, float* u_s, int* err) {
+  __shared__ __align__(128) float4 sW[2][NA_COLS * NA_NT];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
+  const float4* Wt = (const float4*)(W32 + woff32[ti]);
+  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  const bool live = b < B;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  __syncthreads();
+  uint32_t phase0 = 0, phase1 = 0;
+  for (int i0 = 0; i0 < nT; i0 += NA_NT) {
+    const int ni = min(NA_NT, nT - i0);
+    float acc[NA_NT];
+#pragma unroll
+    for (int i = 0; i < NA_NT; i++) acc[i] = 0.f;
+    // W rows of this pass: entries (col, i0 .. i0+ni) are contiguous only when
+    // ni == nT; otherwise copy column by column (rare: leaves with > 32 nodes)
+    const int nchunk = (int)((ncol + NA_COLS - 1) / NA_COLS);
+    auto issue = [&](int k, int buf) {
+      const int64_t cb = (int64_t)k * NA_COLS;
+      const int cc = (ncol - cb < NA_COLS) ? (int)(ncol - cb) : NA_COLS;
+      if (ni == nT) {
+        tma_load(sW[buf], Wt + cb * nT, (uint32_t)(cc * nT * sizeof(float4)), &bar[buf]);
+      } else {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[buf])),
+                     "r"((uint32_t)(cc * ni * sizeof(float4)))
+                     : "memory");
+        for (int c = 0; c < cc; c++)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(&sW[buf][c * ni])),
+              "l"(Wt + (cb + c) * nT + i0), "r"((uint32_t)(ni * sizeof(float4))), "r"(smem_u32(&bar[buf]))
+              : "memory");
+      }
+    };
+    __syncthreads();
+    if (threadIdx.x == 0 && nchunk > 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(0, 0);
+    }
+    for (int k = 0; k < nchunk; k++) {
+      const int buf = k & 1;
+      if (threadIdx.x == 0 && k + 1 < nchunk) issue(k + 1, buf ^ 1);  // buffer buf^1 was released by the sync below
+      const uint32_t ph = buf ? phase1 : phase0;
+      if (!mbar_wait(&bar[buf], ph)) {
+        if (threadIdx.x == 0) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+        mbar_wait(&bar[buf], ph);
+        return;
+      }
+      if (buf)
+        phase1 ^= 1;
+      else
+        phase0 ^= 1;
+      const int64_t cb = (int64_t)k * NA_COLS;
+      const int cc = (ncol - cb < NA_COLS) ? (int)(ncol - cb) : NA_COLS;
+      if (live) {
+        for (int c = 0; c < cc; c++) {
+          const float* mp = Ms + (int64_t)cols[c0 + cb + c] * 3 * B + b;
+          const float mx = mp[0], my = mp[B], mz = mp[2 * B];
+          const float4* w = sW[buf] + c * ni;
+#pragma unroll
+          for (int i = 0; i < NA_NT; i++)
+            if (i < ni) {
+              const float4 wv = w[i];
+              acc[i] = fmaf(wv.x, mx, fmaf(wv.y, my, fmaf(wv.z, mz, acc[i])));
+            }
+        }
+      }
+      __syncthreads();  // everyone is done with buffer buf before it is refilled
+      if (threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < NA_NT; i++)
+        if (i < ni) u_s[(int64_t)(rT.z + i0 + i) * B + b] += acc[i];
+    }
   }
 }
 
@@ -238,9 +373,15 @@ void build_near_field(Plan& P) {
                                             P.tet_geo, P.tet_grad, P.w_coloff, P.w_cols, P.w_off, P.W64);
   DM_LAUNCH("k_near_build");
   if (P.opt.precision != DEMAG_FP64) {
-    P.W32 = dalloc<float>(P, std::max<int64_t>(P.n_wentries, 1));
-    k_f64_to_f32<<<1024, 256, 0, s>>>(P.W64, P.W32, P.n_wentries);
-    DM_LAUNCH("k_f64_to_f32");
+    // FP32 copy, [col][node][4] per target leaf (16-byte entries for the TMA-staged apply)
+    std::vector<int64_t> hw32(nT + 1, 0);
+    for (int64_t ti = 0; ti < nT; ti++) hw32[ti + 1] = hw32[ti] + (hw[ti + 1] - hw[ti]) / 3 * 4;
+    P.w_off32 = dalloc<int64_t>(P, nT + 1);
+    DM_CUDA(cudaMemcpyAsync(P.w_off32, hw32.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    P.W32 = dalloc<float>(P, std::max<int64_t>(hw32[nT], 4));
+    k_pack_w32<<<(unsigned)nT, 256, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_off, P.w_off32, P.W64,
+                                            P.W32);
+    DM_LAUNCH("k_pack_w32");
   }
   DM_CUDA(cudaStreamSynchronize(s));
 }
@@ -253,12 +394,14 @@ void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStre
   DM_LAUNCH("k_near_apply<double>");
 }
 
-void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, cudaStream_t s) {
+void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s) {
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
   if (!nT) return;
-  k_near_apply<float><<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off, P.W32,
-                                                   Ms, B, u_s);
-  DM_LAUNCH("k_near_apply<float>");
+  const int threads = B >= 128 ? 128 : ((B + 31) / 32) * 32;
+  dim3 grid((unsigned)nT, (unsigned)((B + threads - 1) / threads));
+  k_near_apply32<<<grid, threads, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off32, P.W32, Ms, B,
+                                          u_s, err);
+  DM_LAUNCH("k_near_apply32");
 }
 
 }  // namespace demag
