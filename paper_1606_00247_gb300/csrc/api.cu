@@ -23,7 +23,7 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
                      ")"};
 }
 
-StageClock::StageClock(Plan& P_, cudaStream_t s_) : P(P_), s(s_), on(P_.opt.profile != 0) {
+StageClock::StageClock(Plan& P_, cudaStream_t s_, bool allow) : P(P_), s(s_), on(allow && P_.opt.profile != 0) {
   if (on)
     for (auto& e : ev) DM_CUDA(cudaEventCreate(&e));
 }

@@ -157,6 +157,7 @@ struct Plan {
 
   // FP32 far-field operators (mixed precision, per-level scaled)
   float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)
+  int* m2l_sched = nullptr;         // FP32 M2L row schedule (warps x rows), p <= 8
   float* cell_side32 = nullptr;     // per cell side length (float)
 
   std::vector<DevBuf> bufs;
@@ -180,7 +181,7 @@ struct StageClock {
   int launches[DEMAG_N_STAGES] = {};
   bool used[DEMAG_N_STAGES] = {};
   int cur = -1;
-  StageClock(Plan& P_, cudaStream_t s_);
+  StageClock(Plan& P_, cudaStream_t s_, bool allow = true);
   ~StageClock();
   void begin(int stage);
   void end();
@@ -219,6 +220,11 @@ struct Workspace {
   std::vector<void*> ptrs;
 };
 Workspace& workspace(Plan& P, int B);
+// the two drivers on a given workspace (profile_ok = false: no CUDA events are created)
+void eval_fp64_ws(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, cudaStream_t s,
+                  bool profile_ok);
+void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, cudaStream_t s,
+                   bool profile_ok);
 bool is_device_ptr(const void* p);
 // shared FP64 stages (fmm.cu)
 bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, const double** Md, double** ud,
@@ -235,7 +241,8 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
 // mixed-precision far field (fmm32.cu)
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
-bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, cudaStream_t s);  // m2l32.cu
+bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);  // m2l32.cu
+void build_m2l32_schedule(Plan& P);  // m2l32.cu, plan time
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);

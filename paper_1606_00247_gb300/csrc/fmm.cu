@@ -320,7 +320,7 @@ Workspace& workspace(Plan& P, int B) {
     W->L = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
   } else {
     W->Ms32 = (float*)ws_alloc(*W, sizeof(float) * nn * 3 * need);
-    W->Q32 = (float*)ws_alloc(*W, sizeof(float) * ncell * nc * need);
+    W->Q32 = (float*)ws_alloc(*W, sizeof(float) * (ncell * nc * need + 16));  // tail pad for 16-byte bulk copies
     W->L32 = (float*)ws_alloc(*W, sizeof(float) * ncell * nc * need);
     W->u32 = (float*)ws_alloc(*W, sizeof(float) * nn * need);
   }
@@ -344,12 +344,16 @@ bool is_device_ptr(const void* p) {
 }
 
 void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s) {
-  Workspace& W = workspace(P, B);
+  eval_fp64_ws(P, workspace(P, B), M, B, u, H, s, true);
+}
+
+void eval_fp64_ws(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, cudaStream_t s,
+                  bool profile_ok) {
   const double* Md;
   double *ud, *Hd;
   const bool dev = eval_io_begin(P, W, M, B, u, H, &Md, &ud, &Hd, s);
   const int p = P.p, nc = P.nc;
-  StageClock clk(P, s);
+  StageClock clk(P, s, profile_ok);
   clk.begin(DEMAG_STAGE_GATHER);
   k_gather_M<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms);
   DM_LAUNCH("k_gather_M");

@@ -269,16 +269,21 @@ void build_mixed_operators(Plan& P) {
                                                              P.nc1, P.Ghat32);
     DM_LAUNCH("k_ghat32");
   }
+  build_m2l32_schedule(P);
 }
 
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s) {
-  Workspace& W = workspace(P, B);
+  eval_mixed_ws(P, workspace(P, B), M, B, u, H, s, true);
+}
+
+void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, cudaStream_t s,
+                   bool profile_ok) {
   const double* Md;
   double *ud, *Hd;
   const bool dev = eval_io_begin(P, W, M, B, u, H, &Md, &ud, &Hd, s);
   const bool otf = P.opt.near_mode == 0;
   const int p = P.p, nc = P.nc;
-  StageClock clk(P, s);
+  StageClock clk(P, s, profile_ok);
   clk.begin(DEMAG_STAGE_GATHER);
   k_gather_M32<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms32, otf ? W.Ms : nullptr);
   DM_LAUNCH("k_gather_M32");
@@ -304,7 +309,7 @@ void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStrea
   clk.begin(DEMAG_STAGE_M2L);
   DM_CUDA(cudaMemsetAsync(W.L32, 0, sizeof(float) * P.ncells * nc * B, s));
   if (P.h_m2l_targets.empty()) {
-  } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, s)) {
+  } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s)) {
     clk.launched();
   } else {
     dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((nc * B + 128 * 8 - 1) / (128 * 8)));

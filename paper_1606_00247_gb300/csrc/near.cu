@@ -211,96 +211,101 @@ constexpr int NA_COLS = 32;  // columns per staged chunk
 constexpr int NA_NT = 32;    // target nodes per pass (registers)
 
 // u[i][b] += sum_col W[col][i] . M[node(col)][.][b]
-// block per (target leaf, 128-state slice); thread = state; all target nodes of
-// the pass in registers; W chunks double-buffered in shared memory by TMA.
-__global__ void __launch_bounds__(128) k_near_apply32(const int32_t* __restrict__ targets,
-                                                      const int4* __restrict__ range,
-                                                      const int64_t* __restrict__ coloff,
-                                                      const int32_t* __restrict__ cols,
-                                                      const int64_t* __restrict__ woff32,
-                                                      const float* __restrict__ W32, const float* __restrict__ Ms,
-                                                      int B, float* u_s, int* err) {
-  __shared__ __align__(128) float4 sW[2][NA_COLS * NA_NT];
-  __shared__ __align__(8) uint64_t bar[2];
+// one block of NA_WARPS warps per (target leaf, 32-state slice); lane =
+// state; warp w takes the column chunks w, w + NA_WARPS, ...; each warp stages
+// its chunk of W ([col][node][4] floats, contiguous) into its own shared-memory
+// area with a TMA bulk copy, gathers M of the chunk's columns (4 columns in
+// flight per lane) and keeps the partial sums of all target nodes of the pass
+// in registers; the warps' partials are added in shared memory at the end.
+constexpr int NA_WARPS = 8;
+
+__global__ void __launch_bounds__(NA_WARPS * 32) k_near_apply32_v2(
+    const int32_t* __restrict__ targets, const int4* __restrict__ range, const int64_t* __restrict__ coloff,
+    const int32_t* __restrict__ cols, const int64_t* __restrict__ woff32, const float* __restrict__ W32,
+    const float* __restrict__ Ms, int B, float* u_s, int* err) {
+  extern __shared__ __align__(128) float4 sWv[];  // NA_WARPS x NA_COLS x NA_NT float4
+  __shared__ __align__(8) uint64_t bar[NA_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ti = blockIdx.x;
   const int4 rT = range[targets[ti]];
   const int nT = rT.w - rT.z;
   const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
   const float4* Wt = (const float4*)(W32 + woff32[ti]);
-  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y * 32 + lane;
   const bool live = b < B;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  uint32_t phase0 = 0, phase1 = 0;
+  const int bb = live ? b : 0;
+  float4* myW = sWv + warp * NA_COLS * NA_NT;
+  float* red = (float*)sWv;  // reused for the reduction: NA_WARPS x NA_NT x 32
+  if (lane == 0) mbar_init(&bar[warp]);
+  __syncwarp();
+  uint32_t phase = 0;
+  const int nchunk = (int)((ncol + NA_COLS - 1) / NA_COLS);
   for (int i0 = 0; i0 < nT; i0 += NA_NT) {
     const int ni = min(NA_NT, nT - i0);
     float acc[NA_NT];
 #pragma unroll
     for (int i = 0; i < NA_NT; i++) acc[i] = 0.f;
-    // W rows of this pass: entries (col, i0 .. i0+ni) are contiguous only when
-    // ni == nT; otherwise copy column by column (rare: leaves with > 32 nodes)
-    const int nchunk = (int)((ncol + NA_COLS - 1) / NA_COLS);
-    auto issue = [&](int k, int buf) {
+    for (int k = warp; k < nchunk; k += NA_WARPS) {
       const int64_t cb = (int64_t)k * NA_COLS;
       const int cc = (ncol - cb < NA_COLS) ? (int)(ncol - cb) : NA_COLS;
-      if (ni == nT) {
-        tma_load(sW[buf], Wt + cb * nT, (uint32_t)(cc * nT * sizeof(float4)), &bar[buf]);
-      } else {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[buf])),
-                     "r"((uint32_t)(cc * ni * sizeof(float4)))
-                     : "memory");
-        for (int c = 0; c < cc; c++)
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  smem_u32(&sW[buf][c * ni])),
-              "l"(Wt + (cb + c) * nT + i0), "r"((uint32_t)(ni * sizeof(float4))), "r"(smem_u32(&bar[buf]))
-              : "memory");
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (ni == nT) {
+          tma_load(myW, Wt + cb * nT, (uint32_t)(cc * nT * sizeof(float4)), &bar[warp]);
+        } else {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[warp])),
+                       "r"((uint32_t)(cc * ni * sizeof(float4)))
+                       : "memory");
+          for (int c = 0; c < cc; c++)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(&myW[c * ni])),
+                "l"(Wt + (cb + c) * nT + i0), "r"((uint32_t)(ni * sizeof(float4))), "r"(smem_u32(&bar[warp]))
+                : "memory");
+        }
       }
-    };
-    __syncthreads();
-    if (threadIdx.x == 0 && nchunk > 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(0, 0);
-    }
-    for (int k = 0; k < nchunk; k++) {
-      const int buf = k & 1;
-      if (threadIdx.x == 0 && k + 1 < nchunk) issue(k + 1, buf ^ 1);  // buffer buf^1 was released by the sync below
-      const uint32_t ph = buf ? phase1 : phase0;
-      if (!mbar_wait(&bar[buf], ph)) {
-        if (threadIdx.x == 0) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
-        mbar_wait(&bar[buf], ph);
+      if (!mbar_wait(&bar[warp], phase)) {
+        if (lane == 0) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+        mbar_wait(&bar[warp], phase);
         return;
       }
-      if (buf)
-        phase1 ^= 1;
-      else
-        phase0 ^= 1;
-      const int64_t cb = (int64_t)k * NA_COLS;
-      const int cc = (ncol - cb < NA_COLS) ? (int)(ncol - cb) : NA_COLS;
-      if (live) {
-        for (int c = 0; c < cc; c++) {
-          const float* mp = Ms + (int64_t)cols[c0 + cb + c] * 3 * B + b;
-          const float mx = mp[0], my = mp[B], mz = mp[2 * B];
-          const float4* w = sW[buf] + c * ni;
+      phase ^= 1;
+      for (int c = 0; c < cc; c += 4) {
+        float m[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int cu = (c + u < cc) ? c + u : c;
+          const float* mp = Ms + (int64_t)cols[c0 + cb + cu] * 3 * B + bb;
+          m[u][0] = mp[0];
+          m[u][1] = mp[B];
+          m[u][2] = mp[2 * B];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (c + u >= cc) break;
+          const float4* w = myW + (c + u) * ni;
 #pragma unroll
           for (int i = 0; i < NA_NT; i++)
             if (i < ni) {
               const float4 wv = w[i];
-              acc[i] = fmaf(wv.x, mx, fmaf(wv.y, my, fmaf(wv.z, mz, acc[i])));
+              acc[i] = fmaf(wv.x, m[u][0], fmaf(wv.y, m[u][1], fmaf(wv.z, m[u][2], acc[i])));
             }
         }
       }
-      __syncthreads();  // everyone is done with buffer buf before it is refilled
-      if (threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (live) {
+    // add the warps' partial sums
+    __syncthreads();
 #pragma unroll
-      for (int i = 0; i < NA_NT; i++)
-        if (i < ni) u_s[(int64_t)(rT.z + i0 + i) * B + b] += acc[i];
+    for (int i = 0; i < NA_NT; i++)
+      if (i < ni) red[(warp * NA_NT + i) * 32 + lane] = acc[i];
+    __syncthreads();
+    for (int i = warp; i < ni; i += NA_WARPS) {
+      float v = 0.f;
+      for (int w = 0; w < NA_WARPS; w++) v += red[(w * NA_NT + i) * 32 + lane];
+      if (live) u_s[(int64_t)(rT.z + i0 + i) * B + b] += v;
     }
+    __syncthreads();
   }
 }
 
@@ -397,11 +402,16 @@ void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStre
 void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s) {
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
   if (!nT) return;
-  const int threads = B >= 128 ? 128 : ((B + 31) / 32) * 32;
-  dim3 grid((unsigned)nT, (unsigned)((B + threads - 1) / threads));
-  k_near_apply32<<<grid, threads, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off32, P.W32, Ms, B,
-                                          u_s, err);
-  DM_LAUNCH("k_near_apply32");
+  const size_t smem = sizeof(float4) * NA_WARPS * NA_COLS * NA_NT;
+  static bool attr = false;
+  if (!attr) {
+    DM_CUDA(cudaFuncSetAttribute(k_near_apply32_v2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)nT, (unsigned)((B + 31) / 32));
+  k_near_apply32_v2<<<grid, NA_WARPS * 32, smem, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off32,
+                                                      P.W32, Ms, B, u_s, err);
+  DM_LAUNCH("k_near_apply32_v2");
 }
 
 }  // namespace demag
