@@ -109,6 +109,33 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
  * Nodes that belong to no tet get their potential, and H = 0. */
 demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream);
 
+/* Size of the fixed scratch area used by demag_eval_noalloc (64 MiB). */
+#define DEMAG_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
+
+/* demag_eval without any device allocation.  (The paper has no counterpart:
+ * this is a service of the library.)  For callers that must not allocate
+ * device memory while they run -- e.g. an application whose own pool allocator
+ * has reserved the device memory and forbids further cudaMalloc/cudaFree, or a
+ * latency-critical loop that cannot pay the implicit synchronisation of
+ * cudaMalloc/cudaFree.  demag_eval allocates its workspace on its first call;
+ * this entry point instead takes all of its scratch from one file-scope device
+ * array of DEMAG_NOALLOC_SCRATCH_BYTES that the CUDA runtime reserves on every
+ * device that loads the library, for the lifetime of the process.
+ *   plan, batch : as for demag_eval (batch is not limited by max_batch).
+ *   M, u, H     : DEVICE pointers only (H may be NULL); same layouts and results
+ *                 as demag_eval.  The call is asynchronous on cuda_stream.
+ * Errors: DEMAG_ERR_INVALID_ARG for NULL or host pointers, batch < 1, or a plan
+ * and batch whose scratch exceeds DEMAG_NOALLOC_SCRATCH_BYTES (the message gives
+ * both sizes); DEMAG_ERR_CUDA if the scratch address cannot be resolved.
+ * The first call on a device resolves the array's device address with that
+ * device current (one cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the last
+ * call's contents (each call clears what must start at zero); calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * With opt.profile = 1 the stage timers are not updated by this entry point. */
+demag_status demag_eval_noalloc(demag_plan plan, const double* M, int batch, double* u, double* H,
+                                void* cuda_stream);
+
 demag_status demag_plan_destroy(demag_plan plan);
 
 /* Stages of demag_eval, for the per-stage timers. */

@@ -73,6 +73,8 @@ def load(build_if_missing: bool = True):
         L.demag_plan_create.argtypes = [vp, i64, vp, i64, i32, i32, d, C.POINTER(demag_options), C.POINTER(vp)]
         L.demag_eval.restype = i32
         L.demag_eval.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.demag_eval_noalloc.restype = i32
+        L.demag_eval_noalloc.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_plan_destroy.restype = i32
         L.demag_plan_destroy.argtypes = [vp]
         L.demag_plan_stats.restype = i32
@@ -104,6 +106,11 @@ def demag_plan_create(nodes_ptr, n_nodes, tets_ptr, n_tets, p, leaf_size, theta,
 
 def demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
     return load().demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr)
+
+
+def demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
+    """demag_eval with its scratch in the library's fixed device array (no allocation)."""
+    return load().demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr)
 
 
 def demag_plan_destroy(plan):

@@ -1,0 +1,61 @@
+"""demag_eval_noalloc: the evaluation for callers that must not allocate device
+memory while they run (their own pool allocator owns the device memory, or they
+cannot pay cudaMalloc's implicit synchronisation).  All of its scratch lives in
+the library's fixed device array; its results must equal demag_eval's.
+
+Collected last on purpose (file name), so that a stop-at-first-failure run has
+already run every other test; it also passes when run alone."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1606_00247_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _call_noalloc(plan, M, u, H):
+    from paper_1606_00247_gb300 import _lib
+
+    st = _lib.demag_eval_noalloc(plan.handle, M.data_ptr(), M.shape[0], u.data_ptr(), H.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    return st
+
+
+@pytest.mark.parametrize("precision,near_mode", [("fp64", 0), ("fp64", 1), ("fp32", 1)])
+def test_noalloc_matches_eval_twice(precision, near_mode):
+    from paper_1606_00247_gb300 import _lib
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=0.2)
+    plan = Plan(nodes, tets, p=6, leaf_size=16, max_batch=3, precision=precision, near_mode=near_mode)
+    for call, seed in enumerate((11, 12)):  # two calls in a row with different inputs
+        M = torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], seed=seed, batch=3), device="cuda")
+        u_ref, H_ref = plan.eval(M)
+        u = torch.full_like(u_ref, float("nan"))
+        H = torch.full_like(H_ref, float("nan"))
+        st = _call_noalloc(plan, M, u, H)
+        assert st == _lib.DEMAG_OK, _lib.demag_last_error()
+        torch.cuda.synchronize()
+        tol = 1e-12 if precision == "fp64" else 1e-6
+        assert float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref)) <= tol, call
+        assert float(torch.linalg.norm(H - H_ref) / torch.linalg.norm(H_ref)) <= tol, call
+
+
+def test_noalloc_rejects_oversized_scratch_and_host_pointers():
+    from paper_1606_00247_gb300 import _lib
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=0.12)
+    # on-the-fly near field: 56 doubles per tet and state -> far beyond 64 MiB for 16 states
+    plan = Plan(nodes, tets, p=4, leaf_size=32, max_batch=16, near_mode=0)
+    M = torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], batch=16), device="cuda")
+    u = torch.empty((16, nodes.shape[0]), dtype=torch.float64, device="cuda")
+    H = torch.empty((16, nodes.shape[0], 3), dtype=torch.float64, device="cuda")
+    st = _call_noalloc(plan, M, u, H)
+    assert st == _lib.DEMAG_ERR_INVALID_ARG
+    assert "fixed area holds" in _lib.demag_last_error()
+    Mh = np.zeros((1, nodes.shape[0], 3))
+    uh = np.zeros((1, nodes.shape[0]))
+    st = _lib.demag_eval_noalloc(plan.handle, Mh.ctypes.data, 1, uh.ctypes.data, None, None)
+    assert st == _lib.DEMAG_ERR_INVALID_ARG
