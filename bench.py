@@ -192,6 +192,16 @@ def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
     elif dom == "p2p":
         work = 2.0 * 3 * stats["n_near_cols"] * B / launches_per_eval
         note = f"near-field application, 2 flops per stored coefficient per state, {kind}"
+    if work is not None and dom == "m2l" and precision == "tf32":
+        # tcgen05 kind::tf32: peak = measured dense BF16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        achieved = work / per_launch_s / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+        out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x 1.1/2.25 nominal TF32 ratio",
+                    "note": "algorithmic flops 2*C(p+6,6) per pair per state; the level-blocked tiles execute "
+                            "about 2.2x that on the tensor pipe at p=8"})
+        return out
     if work is not None:
         achieved = work / per_launch_s / 1e12
         peak = alu_peak_tflops(kind, sm_mhz)

@@ -128,8 +128,6 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X3)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
-    if (o.precision == DEMAG_MIXED_TF32 || o.precision == DEMAG_MIXED_BF16X3)
-      fail(DEMAG_ERR_UNSUPPORTED, "tensor-core M2L modes are not built in this version");
     P = new demag_plan_s();
     P->opt = o;
     P->p = o.p;

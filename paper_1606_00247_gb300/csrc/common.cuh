@@ -156,9 +156,7 @@ struct Plan {
   float* W32 = nullptr;
 
   // FP32 far-field operators (mixed precision, per-level scaled)
-  float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)
-  int* m2l_sched = nullptr;         // FP32 M2L row schedule (warps x rows), p <= 8
-  float* cell_side32 = nullptr;     // per cell side length (float)
+  float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)  float* cell_side32 = nullptr;     // per cell side length (float)
 
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
@@ -242,7 +240,7 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);  // m2l32.cu
-void build_m2l32_schedule(Plan& P);  // m2l32.cu, plan time
+bool launch_m2l_tc(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);      // m2l_tc.cu
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);

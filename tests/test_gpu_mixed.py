@@ -62,6 +62,26 @@ def test_mixed_vs_fp64(orc, near_mode, p):
     assert eu < 2e-6 and eh < 2e-5, (eu, eh)
 
 
+@pytest.mark.parametrize("B", [4, 128, 160])
+@pytest.mark.parametrize("p", [4, 6, 8])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_tensor_core_m2l_vs_fp64(prec, p, B):
+    """M2L on tcgen05 tensor cores (FP32 accumulation in tensor memory): full
+    and partial 128-state tiles, against the FP64 path.  Split-BF16 x3 (16
+    significant bits per operand) is held to the mixed-path bar of 1e-4; single
+    TF32 (11 bits) leaves ~2e-4 on u and is checked at 1e-3."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=B)
+    u64, H64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1).eval(M)
+    utc, Htc = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision=prec).eval(M)
+    eu = per_state(utc.cpu().numpy(), u64.cpu().numpy())
+    eh = per_state(Htc.cpu().numpy(), H64.cpu().numpy())
+    bar = 1e-4 if prec == "bf16x3" else 1e-3
+    assert eu <= bar and eh <= bar, (eu, eh)
+    if prec == "bf16x3":
+        assert eu < 5e-5 and eh < 5e-5, (eu, eh)
+
+
 @pytest.mark.parametrize("scale", [1e-3, 1e3])
 def test_mixed_scale_invariance(orc, scale):
     """Per-level scaling keeps FP32 in range for any mesh size."""
