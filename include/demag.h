@@ -67,7 +67,11 @@ typedef struct {
                              at plan time and applied at eval (Sec. 3.4 stores
                              the direct-interaction coefficients)            */
   int max_batch;       /* largest batch B a demag_eval will be given       */
-  int autotune;        /* reserved, must be 0                              */
+  int autotune;        /* 1: at plan time, time the launch shapes of the
+                             tensor-core M2L (TF32 / split BF16) on this
+                             plan's own interaction lists and keep the
+                             fastest (adds up to ~1 s to demag_plan_create);
+                             0: a fixed default shape                      */
   int profile;         /* 1: time every stage of demag_eval with CUDA events
                           on the eval stream (adds one synchronisation per
                           call); read with demag_plan_stats                  */
@@ -168,6 +172,10 @@ typedef struct {
   int64_t n_evals_profiled;        /* evals accumulated in stage_ms          */
   double stage_ms[DEMAG_N_STAGES]; /* summed per-stage device time (profile=1) */
   int64_t stage_launches[DEMAG_N_STAGES];
+  int64_t n_m2l_ops;     /* distinct M2L translation operators tabulated for
+                            the tensor-core M2L (0: CUDA-core M2L)          */
+  int m2l_kps;           /* tensor-core M2L ring: k-steps per slot          */
+  int m2l_ring_bytes;    /* tensor-core M2L ring: shared memory per CTA     */
 } demag_stats;
 
 demag_status demag_plan_stats(demag_plan plan, demag_stats* out);

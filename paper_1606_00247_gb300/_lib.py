@@ -40,7 +40,8 @@ class demag_stats(C.Structure):
                 ("side", C.c_double), ("scale", C.c_double), ("plan_ms", C.c_double), ("p", C.c_int),
                 ("leaf_size", C.c_int), ("precision", C.c_int), ("near_mode", C.c_int), ("max_batch", C.c_int),
                 ("theta", C.c_double), ("eval_launches", C.c_int64), ("n_evals_profiled", C.c_int64),
-                ("stage_ms", C.c_double * DEMAG_N_STAGES), ("stage_launches", C.c_int64 * DEMAG_N_STAGES)]
+                ("stage_ms", C.c_double * DEMAG_N_STAGES), ("stage_launches", C.c_int64 * DEMAG_N_STAGES),
+                ("n_m2l_ops", C.c_int64), ("m2l_kps", C.c_int), ("m2l_ring_bytes", C.c_int)]
 
 
 class demag_tree_export(C.Structure):

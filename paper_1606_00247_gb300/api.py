@@ -29,7 +29,7 @@ class Plan:
     """Tree, lists and operators of one mesh (demag_plan_create)."""
 
     def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
-                 device="cuda", profile=False):
+                 device="cuda", profile=False, autotune=False):
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
@@ -39,6 +39,7 @@ class Plan:
         opt.near_mode = int(near_mode)
         opt.max_batch = int(max_batch)
         opt.profile = int(bool(profile))
+        opt.autotune = int(bool(autotune))
         with torch.cuda.device(self.device):
             st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
                                         int(leaf_size), float(theta), opt)

@@ -124,7 +124,7 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.leaf_size < 1) fail(DEMAG_ERR_INVALID_ARG, "leaf_size must be >= 1");
     if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
     if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
-    if (o.autotune != 0) fail(DEMAG_ERR_UNSUPPORTED, "autotune is reserved");
+    if (o.autotune != 0 && o.autotune != 1) fail(DEMAG_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X3)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
@@ -201,6 +201,9 @@ demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
     o->stage_ms[k] = plan->stage_ms[k];
     o->stage_launches[k] = plan->stage_launches[k];
   }
+  o->n_m2l_ops = plan->n_tc_ops;
+  o->m2l_kps = plan->tc_kps;
+  o->m2l_ring_bytes = plan->tc_budget;
   return DEMAG_OK;
 }
 

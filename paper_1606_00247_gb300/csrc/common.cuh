@@ -155,6 +155,13 @@ struct Plan {
   int64_t* w_off32 = nullptr;       // nT + 1, in floats; W32 is [col][node][4]
   float* W32 = nullptr;
 
+  // tensor-core M2L (TF32 / split BF16): one operator tile set per distinct
+  // (level difference, lattice offset) and the operator index of every pair
+  int64_t n_tc_ops = 0;
+  unsigned char* tc_ops = nullptr;
+  int32_t* m2l_op = nullptr;        // n_m2l
+  int tc_kps = 0, tc_budget = 0;    // ring shape of the M2L kernel: k-steps per slot, ring bytes
+
   // FP32 far-field operators (mixed precision, per-level scaled)
   float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)  float* cell_side32 = nullptr;     // per cell side length (float)
 
@@ -213,6 +220,7 @@ struct Workspace {
   int B = 0;
   double *Ms = nullptr, *Q = nullptr, *L = nullptr, *u_s = nullptr, *state = nullptr;
   float *Ms32 = nullptr, *Q32 = nullptr, *L32 = nullptr, *u32 = nullptr;
+  unsigned char* QP = nullptr;  // moments in the tensor-core tile layout (TF32 / split BF16 M2L)
   double *M_dev = nullptr, *u_dev = nullptr, *H_dev = nullptr;  // staging for host pointers
   int* err = nullptr;
   std::vector<void*> ptrs;
@@ -240,7 +248,12 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);  // m2l32.cu
-bool launch_m2l_tc(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);      // m2l_tc.cu
+// tensor-core M2L (m2l_tc.cu): operator table at plan time; bytes of the packed
+// moments for B states (0 when the tensor-core M2L is off); packs Q into QP and
+// runs the M2L (false: not available for this plan, use the CUDA-core M2L)
+void build_m2l_tc(Plan& P);
+size_t m2l_tc_pack_bytes(const Plan& P, int B);
+bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, int* err, cudaStream_t s);
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);

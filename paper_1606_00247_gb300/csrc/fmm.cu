@@ -323,6 +323,8 @@ Workspace& workspace(Plan& P, int B) {
     W->Q32 = (float*)ws_alloc(*W, sizeof(float) * (ncell * nc * need + 16));  // tail pad for 16-byte bulk copies
     W->L32 = (float*)ws_alloc(*W, sizeof(float) * ncell * nc * need);
     W->u32 = (float*)ws_alloc(*W, sizeof(float) * nn * need);
+    const size_t qp = m2l_tc_pack_bytes(P, need);
+    if (qp) W->QP = (unsigned char*)ws_alloc(*W, qp);
   }
   W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);
   if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);

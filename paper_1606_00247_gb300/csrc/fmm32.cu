@@ -269,6 +269,7 @@ void build_mixed_operators(Plan& P) {
                                                              P.nc1, P.Ghat32);
     DM_LAUNCH("k_ghat32");
   }
+  build_m2l_tc(P);
 }
 
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s) {
@@ -309,8 +310,8 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   DM_CUDA(cudaMemsetAsync(W.L32, 0, sizeof(float) * P.ncells * nc * B, s));
   if (P.h_m2l_targets.empty()) {
   } else if ((P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3) &&
-             launch_m2l_tc(P, B, W.Q32, W.L32, W.err, s)) {
-    clk.launched();
+             launch_m2l_tc(P, B, W.Q32, W.QP, W.L32, W.err, s)) {
+    clk.launched(2);
   } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s)) {
     clk.launched();
   } else {

@@ -6,31 +6,56 @@
 //   D[b][m] = sum_S sum_n A_S[b][n] K_S[m][n],   A_S[b][n] = Qt^S_n(state b),
 //   K_S[m][n] = b_{n+m}(v_S) f_S^|n|  (0 where |n| + |m| > p),
 // accumulated over all sources S of T in tensor memory (M = 128 states = TMEM
-// lanes, N = rows m, K = n).  K_S is triangular in the degrees of (m, n); the
-// rows are cut into level groups [ta, tb) (chosen on the host by a small
-// dynamic programme), group g multiplying only the n with |n| <= p - ta, so
-// that the dense tiles cover ~2.2x the useful entries at p = 8 instead of ~9x.
+// lanes, N = rows m, K = n).
 //
-// Two operand formats:
-//   TF32   : A and K_S rounded to TF32 by the tensor core, one MMA per k-step
-//            (kind::tf32) -- fastest, ~2e-4 relative error on u;
-//   BF16x3 : A = A_hi + A_lo, K = K_hi + K_lo with hi/lo in BF16 (16 significant
-//            bits together), three MMAs per k-step (hi*hi + hi*lo + lo*hi,
-//            kind::f16) -- ~1e-5 relative error on u.
+// Translation operators.  Expansion centres are octree box centres, so
+// v_S = (c_T - c_S) / s_T is fixed by the level difference and an integer
+// lattice offset: 2 v = (2 k_T + 1) - (2 k_S + 1) 2^dl for dl = l_T - l_S >= 0,
+// and 2^(1-dl) v = (2 k_T + 1) 2^-dl - (2 k_S + 1) otherwise (k = integer box
+// coordinates).  A ball of 224k tets has ~5k distinct (dl, offset) keys for
+// ~870k pairs, so every distinct K is built once per plan (FP64 b_k, rounded
+// to the operand format) into a table, and each pair carries the index of its
+// operator.  K is triangular in the degrees of (m, n): rows are cut into
+// level groups [ta, tb) chosen by a small dynamic programme, group g
+// multiplying only the n with |n| <= p - ta (dense tiles cover ~2.6x the
+// useful entries at p = 8 instead of ~9x).
 //
-// Per source the CTA (8 warps) writes A_S (moments of the 128 states) and the
-// group tiles of K_S (operator values from the Taylor-coefficient recurrence of
-// 1/|x|, built for 8 sources at a time) into shared memory in the no-swizzle
-// K-major canonical layout (8-row x 16-byte core matrices, K-adjacent core
-// matrices 128 bytes apart), one thread issues the tcgen05.mma instructions and
-// commits them to an mbarrier, and the operands are rebuilt once the mbarrier
-// reports that the tensor core has consumed them.  The epilogue reads the
-// accumulators with tcgen05.ld and applies sign and scale.  Every wait is
-// bounded: on expiry the kernel records DEMAG_ERR_TIMEOUT, waits once more for
-// its own MMAs, frees its tensor memory and returns.
+// Operand formats:
+//   TF32   : one MMA per k-step (kind::tf32) -- ~2e-4 relative error on u;
+//   BF16x3 : A = A_hi + A_lo, K = K_hi + K_lo in BF16 (16 significant bits
+//            together), three MMAs per k-step (hi*hi + hi*lo + lo*hi,
+//            kind::f16) -- ~3e-5 relative error on u.
+//
+// Data movement.  Before the M2L the moments are repacked (k_m2l_tc_pack)
+// into the tensor-core tile layout, per cell and per 128 states, one 4 KB
+// slice per k-step and operand copy; the operator table is stored in the same
+// per-k-step order.  The M2L kernel is warp-specialised: one thread streams
+// the A slices and the K slices of every source, a few k-steps at a time,
+// into a ring of shared-memory slots with bulk copies (cp.async.bulk,
+// completion on the slot's mbarrier); one thread issues the MMAs of each slot
+// and releases it with tcgen05.commit; four warps read the accumulators at the
+// end (tcgen05.ld) and write L with sign and scale.  The ring runs across
+// source boundaries, so copies and MMAs overlap.  Tiles use the no-swizzle
+// K-major canonical layout (8-row x 16-byte core matrices; the two core
+// matrices of a k-step 128 bytes apart, 8-row groups 256 bytes apart).
+//
+// Issue costs shape the kernel.  On GB300 an M = 128, K = 16 BF16 MMA occupies
+// its issuing CTA for ~60 cycles whatever N <= 112 (N/2 cycles above), and two
+// CTAs per SM overlap about a third of that; one thread's loop overhead adds
+// directly to it.  So the layout is a compile-time constant of the kernel
+// (orders 4, 6, 8, 10): every MMA of a source is unrolled with constant
+// descriptors offsets, and the ring shape (k-steps per slot, slots, CTAs per
+// SM) is chosen at launch -- timed on the plan's own lists when the plan is
+// autotuned.  Other orders run the FP32 CUDA-core M2L.
+//
+// Every wait is bounded: on expiry the kernel records DEMAG_ERR_TIMEOUT, stops
+// issuing, waits (bounded) for its own copies and MMAs in flight, frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -40,40 +65,154 @@ namespace demag {
 namespace {
 
 constexpr int TC_THREADS = 256;
-constexpr int TC_M = 128;  // states per CTA = MMA M = TMEM lanes
-constexpr int TC_BCH = 8;  // sources per operator batch
+constexpr int TC_M = 128;              // states per CTA = MMA M = TMEM lanes
 constexpr int TC_MAXG = 8;
+constexpr int TC_MAXKS = 48;
+constexpr int TC_SLICE = TC_M * 32;    // one k-step of one operand copy: 128 rows x 32 bytes
+constexpr int TC_MAXNC = 512;          // b_k table of the operator build (p <= 12)
 
-struct TcGroups {
-  int ng;
-  int m0[TC_MAXG], nrow[TC_MAXG];  // rows [m0, m0 + nrow) of the graded order
-  int N[TC_MAXG];                  // rows padded to a multiple of 16 (MMA N)
-  int K[TC_MAXG];                  // n count padded to one MMA k-step (32 bytes of K)
-  int col[TC_MAXG];                // first TMEM column of the group
-  int boff[TC_MAXG];               // byte offset of the group's K_S tile in the B area
-  int sbo[TC_MAXG];                // stride between 8-row core-matrix groups of that tile
-  int kmax;                        // padded K of the A tile
-  int sbo_a;                       // stride between 8-row groups of the A tile
-  int a_bytes, b_bytes;            // one copy of the A tile / of all K_S tiles
-  int tmem_cols;                   // power of two >= sum of N
+template <class T>
+struct Tmp {
+  T* p = nullptr;
+  explicit Tmp(size_t n) {
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      fail(DEMAG_ERR_OUT_OF_MEMORY, "M2L tensor-core temporary allocation failed");
+    }
+  }
+  ~Tmp() {
+    if (p) cudaFree(p);
+  }
 };
 
+// ---------------------------------------------------------------------------
+// tile layout of one order and operand format (a compile-time constant of the
+// kernels; also evaluated on the host for the operator table and the packing)
+struct TcLayout {
+  int valid, bf16, ncopy;
+  int E, KW;                        // elements per 16 bytes, per k-step (2E)
+  int ng;                           // level groups, K non-increasing in g
+  int m0[TC_MAXG], nrow[TC_MAXG];   // rows [m0, m0 + nrow) of the graded order
+  int N[TC_MAXG], K[TC_MAXG];       // rows padded to 16 (MMA N), n count padded to a k-step
+  int col[TC_MAXG];                 // first TMEM column of the group
+  int rowpre[TC_MAXG + 1];          // sum of N over the groups before g
+  int KS;                           // k-steps of the A tile (K[0] / KW)
+  int na[TC_MAXKS];                 // groups active at k-step ks (a prefix)
+  int ks_off[TC_MAXKS + 1];         // byte offset of k-step ks within one operator
+  int op_bytes;                     // one operator, all k-steps, all copies
+  int a_bytes;                      // A slice of one k-step, all copies
+  int tmem_cols;                    // power of two >= sum of N
+};
+
+__host__ __device__ constexpr int cnc_of(int t) { return t < 0 ? 0 : (t + 1) * (t + 2) * (t + 3) / 6; }
+__host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// level groups minimise sum over groups of (N_g K_g + 256); then the layout
+__host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16) {
+  TcLayout G{};
+  if (p < 1 || p > 12 || cnc_of(p) > TC_MAXNC) return G;
+  G.bf16 = bf16 ? 1 : 0;
+  G.ncopy = bf16 ? 2 : 1;
+  G.E = bf16 ? 8 : 4;
+  G.KW = 2 * G.E;
+  const int T = p + 1;
+  long best[16] = {};
+  int from[16] = {};
+  for (int i = 0; i <= T; i++) best[i] = -1;
+  best[0] = 0;
+  for (int tb = 1; tb <= T; tb++)  // groups cover degrees [ta, tb)
+    for (int ta = 0; ta < tb; ta++) {
+      if (best[ta] < 0) continue;
+      const long cost = (long)pad_to(cnc_of(tb - 1) - cnc_of(ta - 1), 16) * pad_to(cnc_of(p - ta), G.KW) + 256;
+      if (best[tb] < 0 || best[ta] + cost < best[tb]) {
+        best[tb] = best[ta] + cost;
+        from[tb] = ta;
+      }
+    }
+  int ta_of[16] = {}, tb_of[16] = {}, ng = 0;
+  for (int tb = T; tb > 0; tb = from[tb]) {
+    ta_of[ng] = from[tb];
+    tb_of[ng] = tb;
+    ng++;
+  }
+  if (ng > TC_MAXG) return G;
+  G.ng = ng;
+  int col = 0;
+  for (int g = 0; g < ng; g++) {  // ascending degrees
+    const int ta = ta_of[ng - 1 - g], tb = tb_of[ng - 1 - g];
+    G.m0[g] = cnc_of(ta - 1);
+    G.nrow[g] = cnc_of(tb - 1) - cnc_of(ta - 1);
+    G.N[g] = pad_to(G.nrow[g], 16);
+    if (G.N[g] > 256) return TcLayout{};  // MMA N limit for M = 128
+    G.K[g] = pad_to(cnc_of(p - ta), G.KW);
+    G.col[g] = col;
+    G.rowpre[g] = col;
+    col += G.N[g];
+  }
+  G.rowpre[ng] = col;
+  G.KS = G.K[0] / G.KW;
+  if (G.KS > TC_MAXKS) return TcLayout{};
+  G.ks_off[0] = 0;
+  for (int ks = 0; ks < G.KS; ks++) {
+    int na = 0;
+    while (na < ng && G.K[na] > ks * G.KW) na++;
+    G.na[ks] = na;
+    G.ks_off[ks + 1] = G.ks_off[ks] + G.ncopy * 32 * G.rowpre[na];
+  }
+  G.op_bytes = G.ks_off[G.KS];
+  G.a_bytes = G.ncopy * TC_SLICE;
+  int tc = 32;
+  while (tc < col) tc *= 2;
+  if (tc > 512) return TcLayout{};
+  G.tmem_cols = tc;
+  G.valid = 1;
+  return G;
+}
+
+// the orders with a compiled tensor-core kernel
+constexpr bool tc_order(int p) { return p == 4 || p == 6 || p == 8 || p == 10; }
+
+// ring shape of one launch: `kps` k-steps of one source per slot
+struct TcRing {
+  int kps, nsteps, slot_bytes, nslots;
+  int step_koff[TC_MAXKS], step_kb[TC_MAXKS];  // K bytes of step st within one operator
+};
+
+bool make_ring(const TcLayout& G, int kps, int budget, TcRing& R) {
+  if (!G.valid || kps < 1 || kps > G.KS) return false;
+  R = TcRing{};
+  R.kps = kps;
+  R.nsteps = (G.KS + kps - 1) / kps;
+  int maxk = 0;
+  for (int st = 0; st < R.nsteps; st++) {
+    const int k0 = st * kps, k1 = std::min(k0 + kps, G.KS);
+    R.step_koff[st] = G.ks_off[k0];
+    R.step_kb[st] = G.ks_off[k1] - G.ks_off[k0];
+    maxk = std::max(maxk, R.step_kb[st]);
+  }
+  R.slot_bytes = pad_to(kps * G.a_bytes + maxk, 1024);
+  R.nslots = std::min(32, budget / R.slot_bytes);
+  return R.nslots >= 2;
+}
+
+size_t ring_smem(const TcRing& R) { return (size_t)R.nslots * R.slot_bytes + sizeof(uint64_t) * (2 * R.nslots + 1) + 64; }
+
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ int tri3(int t) { return t * (t + 1) * (t + 2) / 6; }
-__device__ __forceinline__ int tri2(int j) { return j * (j + 1) / 2; }
-__device__ __forceinline__ int idx3(int a, int b, int c) { return tri3(a + b + c) + tri2(b + c) + c; }
-
-// shared-memory matrix descriptor: no swizzle, K-major canonical layout
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
-  return d;                // base offset 0, relative LBO, swizzle none
+__host__ __device__ constexpr int tri3(int t) { return t * (t + 1) * (t + 2) / 6; }
+__host__ __device__ constexpr int idx3(int a, int b, int c) {
+  return tri3(a + b + c) + (b + c) * (b + c + 1) / 2 + c;
 }
-// instruction descriptors: D F32, A and B K-major; format 2 = TF32, 1 = BF16
+
+// shared-memory matrix descriptor, no swizzle, K-major canonical layout:
+// LBO = 128 bytes between the two core matrices of a k-step, SBO = 256 bytes
+// between 8-row groups, descriptor version 1 (bit 46); the start address
+// (>> 4, 14 bits) is or-ed in
+constexpr uint64_t DESC_FIXED = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return DESC_FIXED | (uint64_t)((saddr & 0x3FFFFu) >> 4); }
+
+// instruction descriptor: D F32, A and B K-major; format 2 = TF32, 1 = BF16
 __host__ __device__ constexpr uint32_t idesc(int fmt, int M, int N) {
   return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
@@ -81,20 +220,33 @@ __host__ __device__ constexpr uint32_t idesc(int fmt, int M, int N) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (long it = 0; it < (1l << 24); it++) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    if (ok) return true;
-    if (it > 64) __nanosleep(32);
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; gives up early when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
+  if (mbar_test(bar, phase)) return true;
+  for (int it = 0; it < (1 << 24); it++) {
+    if (mbar_test(bar, phase)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (it > 64) __nanosleep(64);
   }
   return false;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 template <bool BF16>
@@ -112,9 +264,8 @@ __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bde
         "l"(adesc), "l"(bdesc), "r"(id), "r"(acc)
         : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -128,70 +279,164 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// elements per 16-byte core-matrix row: 4 (TF32 in FP32 containers) or 8 (BF16)
-template <bool BF16>
-constexpr int EPR = BF16 ? 8 : 4;
-
-// byte offset of element (row r, k) in a K-major no-swizzle tile
-template <bool BF16>
-__device__ __forceinline__ int tile_off(int r, int k, int sbo) {
-  return (r >> 3) * sbo + (k / EPR<BF16>)*128 + (r & 7) * 16;
-}
-
-// one 16-byte row of a core matrix: EPR consecutive values of K; BF16x3
+// one 16-byte row of a core matrix (E consecutive values of K): split BF16
 // writes the high part to `hi` and the rounding residual to `lo`
 template <bool BF16>
 __device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, const float* v) {
   if constexpr (BF16) {
-    __align__(16) __nv_bfloat16 h[8], l[8];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      h[u] = __float2bfloat16_rn(v[u]);
-      l[u] = __float2bfloat16_rn(v[u] - __bfloat162float(h[u]));
+    for (int u = 0; u < 4; u++) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+      const float2 hf = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * u] - hf.x, v[2 * u + 1] - hf.y);
+      h[u] = *(const uint32_t*)&hh;
+      l[u] = *(const uint32_t*)&ll;
     }
-    *(uint4*)hi = *(const uint4*)h;
-    *(uint4*)lo = *(const uint4*)l;
+    *(uint4*)hi = make_uint4(h[0], h[1], h[2], h[3]);
+    *(uint4*)lo = make_uint4(l[0], l[1], l[2], l[3]);
   } else {
     (void)lo;
     *(float4*)hi = make_float4(v[0], v[1], v[2], v[3]);
   }
 }
 
+// the same from FP64 values: hi = BF16(v), lo = BF16(v - hi) with the
+// residual taken in FP64 (TF32: the FP32 value, rounded by the tensor core)
 template <bool BF16>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const int32_t* __restrict__ targets,
-                                                        const int64_t* __restrict__ m2l_off,
-                                                        const int32_t* __restrict__ m2l_src,
-                                                        const double* __restrict__ centre,
-                                                        const int32_t* __restrict__ level, double side, int p, int nc,
-                                                        int B, const TcGroups G, const float* __restrict__ Q, float* L,
-                                                        int* err) {
-  constexpr int E = EPR<BF16>;
-  constexpr int NCOPY = BF16 ? 2 : 1;  // hi (+ lo)
+__device__ __forceinline__ void store_row64(unsigned char* hi, unsigned char* lo, const double* v) {
+  if constexpr (BF16) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      h[u] = __float2bfloat16_rn((float)v[u]);
+      l[u] = __float2bfloat16_rn((float)(v[u] - (double)__bfloat162float(h[u])));
+    }
+    *(uint4*)hi = *(const uint4*)h;
+    *(uint4*)lo = *(const uint4*)l;
+  } else {
+    (void)lo;
+    *(float4*)hi = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// moments -> tile layout: QP[cell][sb][ks][copy][128 rows x 32 bytes]
+template <bool BF16>
+__global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ Q, int nc, int B, int nsb, int KS,
+                                                      int a_bytes, unsigned char* __restrict__ QP) {
+  constexpr int E = BF16 ? 8 : 4;
+  const int64_t cell = blockIdx.x;
+  const int sb = blockIdx.y, b = threadIdx.x, bb = sb * TC_M + b;
+  const bool alive = bb < B;
+  const float* q = Q + cell * nc * (int64_t)B + bb;
+  unsigned char* out = QP + (cell * nsb + sb) * (int64_t)KS * a_bytes;
+  for (int qq = 0; qq < 2 * KS; qq++) {
+    float v[E];
+#pragma unroll
+    for (int u = 0; u < E; u++) {
+      const int n = qq * E + u;
+      v[u] = (alive && n < nc) ? q[(int64_t)n * B] : 0.f;
+    }
+    const int off = (qq >> 1) * a_bytes + (b >> 3) * 256 + (qq & 1) * 128 + (b & 7) * 16;
+    store_row<BF16>(out + off, out + off + TC_SLICE, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operator table: key = (dl, I) with v = I * 2^-(max(0, -dl) + 1), f = 2^dl
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_m2l_tc_ops(const int4* __restrict__ keys, int p, int nc, const TcLayout G,
+                                                    unsigned char* __restrict__ ops) {
+  constexpr int E = BF16 ? 8 : 4;
+  __shared__ double b[TC_MAXNC];
+  const int tid = threadIdx.x;
+  const int4 key = keys[blockIdx.x];
+  const int dl = key.x;
+  const double sc = ldexp(1.0, -((dl < 0 ? -dl : 0) + 1));
+  const double vx = key.y * sc, vy = key.z * sc, vz = key.w * sc, r2 = vx * vx + vy * vy + vz * vz;
+  if (tid == 0) b[0] = 1.0 / sqrt(r2);
+  __syncthreads();
+  // b_k = (-1)^|k| d^k (1/|x|) at v:  |k| r^2 b_k = (2|k|-1) sum k_i v_i b_{k-e_i} - (|k|-1) sum k_i (k_i-1) b_{k-2e_i}
+  for (int t = 1; t <= p; t++) {
+    for (int k = tri3(t) + tid; k < tri3(t + 1); k += blockDim.x) {
+      int ka, kb, kz;
+      mi_decode(k, ka, kb, kz);
+      double s1 = 0.0, s2 = 0.0;
+      if (ka) s1 += ka * vx * b[idx3(ka - 1, kb, kz)];
+      if (kb) s1 += kb * vy * b[idx3(ka, kb - 1, kz)];
+      if (kz) s1 += kz * vz * b[idx3(ka, kb, kz - 1)];
+      if (ka > 1) s2 += ka * (ka - 1) * b[idx3(ka - 2, kb, kz)];
+      if (kb > 1) s2 += kb * (kb - 1) * b[idx3(ka, kb - 2, kz)];
+      if (kz > 1) s2 += kz * (kz - 1) * b[idx3(ka, kb, kz - 2)];
+      b[k] = ((2 * t - 1) * s1 - (t - 1) * s2) / (t * r2);
+    }
+    __syncthreads();
+  }
+  unsigned char* out = ops + (int64_t)blockIdx.x * G.op_bytes;
+  for (int ks = 0; ks < G.KS; ks++) {
+    unsigned char* chunk = out + G.ks_off[ks];
+    for (int g = 0; g < G.na[ks]; g++) {
+      unsigned char* tile = chunk + G.ncopy * 32 * G.rowpre[g];
+      for (int it = tid; it < 2 * G.N[g]; it += blockDim.x) {
+        const int r = it >> 1, kc = it & 1;
+        double v[E];
+        for (int u = 0; u < E; u++) {
+          v[u] = 0.0;
+          const int n = ks * G.KW + kc * E + u;
+          if (r < G.nrow[g] && n < nc) {
+            int ma, mb, mz, na, nb, nz;
+            mi_decode(G.m0[g] + r, ma, mb, mz);
+            mi_decode(n, na, nb, nz);
+            const int tn = na + nb + nz;
+            if (tn + ma + mb + mz <= p) v[u] = b[idx3(na + ma, nb + mb, nz + mz)] * ldexp(1.0, dl * tn);
+          }
+        }
+        const int off = (r >> 3) * 256 + kc * 128 + (r & 7) * 16;
+        store_row64<BF16>(tile + off, tile + 32 * G.N[g] + off, v);
+      }
+    }
+  }
+}
+
+// degree of the multi-index at position m of the graded order
+__host__ __device__ constexpr int degree_of(int m) {
+  int t = 0;
+  while (tri3(t + 1) <= m) t++;
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+template <int P, bool BF16>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_m2l_tc(const int32_t* __restrict__ targets, const int64_t* __restrict__ m2l_off,
+             const int32_t* __restrict__ m2l_src, const int32_t* __restrict__ m2l_op,
+             const int32_t* __restrict__ level, double side, int nc, int B, int nsb, const TcRing R,
+             const unsigned char* __restrict__ QP, const unsigned char* __restrict__ ops, float* L, int* err) {
+  constexpr TcLayout G = tc_layout(P, BF16);
+  static_assert(G.valid, "no tensor-core layout for this order");
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* As = sm;                               // A tile(s): 128 states x kmax
-  unsigned char* Bs = As + NCOPY * G.a_bytes;           // group tiles of K_S (hi, then lo)
-  float* bks = (float*)(Bs + NCOPY * G.b_bytes);        // TC_BCH x nc operator vectors
-  float* fps = bks + TC_BCH * nc;                       // TC_BCH x 16
-  float* geo = fps + TC_BCH * 16;                       // TC_BCH x 4
-  int* mi = (int*)(geo + TC_BCH * 4);                   // nc packed multi-indices
-  uint64_t* bar = (uint64_t*)(mi + ((nc + 1) & ~1));
-  uint32_t* tmem_slot = (uint32_t*)(bar + 1);
-  int* abort_flag = (int*)(tmem_slot + 1);
+  uint64_t* full = (uint64_t*)(sm + (size_t)R.nslots * R.slot_bytes);
+  uint64_t* empty = full + R.nslots;
+  uint64_t* done = empty + R.nslots;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int* counts = (int*)(tmem_slot + 2);  // slots issued, slots consumed
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int32_t T = targets[blockIdx.x];
-  const int b0 = blockIdx.y * TC_M;
-  const double sT = ldexp(side, -level[T]);
-  const double cx = centre[3 * T], cy = centre[3 * T + 1], cz = centre[3 * T + 2];
-  for (int i = tid; i < nc; i += blockDim.x) {
-    int a, b, c;
-    mi_decode(i, a, b, c);
-    mi[i] = a | (b << 8) | (c << 16) | ((a + b + c) << 24);
-  }
+  const int sb = blockIdx.y;
+  const int64_t e0 = m2l_off[T], e1 = m2l_off[T + 1];
   if (tid == 0) {
-    mbar_init(bar);
+    for (int i = 0; i < R.nslots; i++) {
+      mbar_init(&full[i]);
+      mbar_init(&empty[i]);
+    }
+    mbar_init(done);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
+    counts[0] = counts[1] = 0;
   }
-  if (warp == 0) {  // tensor memory for the accumulators of all groups
+  if (warp == 2) {  // tensor memory for the accumulators of all groups
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(G.tmem_cols)
                  : "memory");
@@ -201,232 +446,344 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const int32_t* __restr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t phase = 0;
-  bool first = true;
-  const int64_t e0 = m2l_off[T], e1 = m2l_off[T + 1];
-  for (int64_t ec = e0; ec < e1; ec += TC_BCH) {
-    const int ns = (e1 - ec < TC_BCH) ? (int)(e1 - ec) : TC_BCH;
-    if (tid < ns) {
-      const int32_t S = m2l_src[ec + tid];
-      const float x = (float)((cx - centre[3 * S]) / sT), y = (float)((cy - centre[3 * S + 1]) / sT),
-                  z = (float)((cz - centre[3 * S + 2]) / sT);
-      float* g = geo + 4 * tid;
-      g[0] = x;
-      g[1] = y;
-      g[2] = z;
-      g[3] = x * x + y * y + z * z;
-      bks[tid * nc] = rsqrtf(g[3]);
-      const int dl = level[T] - level[S];
-      for (int t = 0; t <= p; t++) fps[tid * 16 + t] = ldexpf(1.f, dl * t);
-    }
-    __syncthreads();
-    for (int t = 1; t <= p; t++) {
-      const int o = tri3(t), cnt = (t + 1) * (t + 2) / 2;
-      for (int q = tid; q < ns * cnt; q += blockDim.x) {
-        const int s = q / cnt, k = o + (q - s * cnt);
-        const int kk = mi[k], ka = kk & 255, kb = (kk >> 8) & 255, kz = (kk >> 16) & 255;
-        const float* g = geo + 4 * s;
-        const float* bb = bks + s * nc;
-        float s1 = 0.f, s2 = 0.f;
-        if (ka) s1 += ka * g[0] * bb[idx3(ka - 1, kb, kz)];
-        if (kb) s1 += kb * g[1] * bb[idx3(ka, kb - 1, kz)];
-        if (kz) s1 += kz * g[2] * bb[idx3(ka, kb, kz - 1)];
-        if (ka > 1) s2 += ka * (ka - 1) * bb[idx3(ka - 2, kb, kz)];
-        if (kb > 1) s2 += kb * (kb - 1) * bb[idx3(ka, kb - 2, kz)];
-        if (kz > 1) s2 += kz * (kz - 1) * bb[idx3(ka, kb, kz - 2)];
-        bks[s * nc + k] = ((2 * t - 1) * s1 - (t - 1) * s2) / (t * g[3]);
-      }
-      __syncthreads();
-    }
-    for (int s = 0; s < ns; s++) {
-      const int32_t S = m2l_src[ec + s];
-      // ---- A_S: moments of the 128 states, E consecutive n per 16-byte row
-      {
-        const float* Qs = Q + (int64_t)S * nc * B + b0;
-        const int b = tid & (TC_M - 1);
-        const bool live = b0 + b < B;
-        for (int q = tid >> 7; q < G.kmax / E; q += TC_THREADS / TC_M) {
-          float v[E];
-#pragma unroll
-          for (int u = 0; u < E; u++) {
-            const int n = E * q + u;
-            v[u] = (live && n < nc) ? Qs[(int64_t)n * B + b] : 0.f;
-          }
-          const int off = tile_off<BF16>(b, E * q, G.sbo_a);
-          store_row<BF16>(As + off, As + G.a_bytes + off, v);
+  const uint32_t ring0 = smem_u32(sm), full0 = smem_u32(full), empty0 = smem_u32(empty);
+
+  if (warp == 0) {
+    // ---- producer: the A and K slices of every (source, step) into the ring
+    if (lane == 0) {
+      int slot = 0, n = 0;
+      uint32_t phase = 0;
+      int32_t S = m2l_src[e0], O = m2l_op[e0];
+      for (int64_t e = e0; e < e1 && !*abort_flag; e++) {
+        int32_t Sn = 0, On = 0;
+        if (e + 1 < e1) {  // next pair's indices, ahead of their use
+          Sn = m2l_src[e + 1];
+          On = m2l_op[e + 1];
         }
+        const unsigned char* a = QP + ((int64_t)S * nsb + sb) * (int64_t)(G.KS * G.a_bytes);
+        const unsigned char* k = ops + (int64_t)O * G.op_bytes;
+        for (int st = 0; st < R.nsteps; st++) {
+          if (n >= R.nslots && !mbar_wait(empty0 + 8 * slot, phase ^ 1u, abort_flag)) {
+            if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+            *abort_flag = 1;
+            break;
+          }
+          const int k0 = st * R.kps;
+          const uint32_t fb = full0 + 8 * slot, dst = ring0 + slot * R.slot_bytes;
+          const uint32_t ab = (uint32_t)(min(R.kps, G.KS - k0) * G.a_bytes), kb = (uint32_t)R.step_kb[st];
+          expect_tx(fb, ab + kb);
+          bulk_load(dst, a + (int64_t)k0 * G.a_bytes, ab, fb);
+          bulk_load(dst + R.kps * G.a_bytes, k + R.step_koff[st], kb, fb);
+          n++;
+          if (++slot == R.nslots) {
+            slot = 0;
+            phase ^= 1u;
+          }
+        }
+        S = Sn;
+        O = On;
       }
-      // ---- K_S group tiles
-      {
-        const float* bk = bks + s * nc;
-        const float* fp = fps + s * 16;
-        for (int g = 0; g < G.ng; g++) {
-          const int nq = G.K[g] / E, items = G.N[g] * nq;
-          unsigned char* tile = Bs + G.boff[g];
-          for (int it = tid; it < items; it += blockDim.x) {
-            const int q = it / G.N[g], r = it - q * G.N[g];  // consecutive threads: consecutive rows
-            float v[E];
+      counts[0] = n;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issue: one thread; the MMAs of a source are unrolled
+    if (lane == 0) {
+      int slot = 0, n = 0;
+      uint32_t phase = 0, acc = 0;  // acc = 0: the first k-step of the first source overwrites D
+      bool bad = false;
+      for (int64_t e = e0; e < e1 && !bad; e++) {
+        int j = 0;
+        uint32_t sa = 0, kb0 = 0;
 #pragma unroll
-            for (int u = 0; u < E; u++) v[u] = 0.f;
-            if (r < G.nrow[g]) {
-              const int mm = mi[G.m0[g] + r];
-              const int ma = mm & 255, mb = (mm >> 8) & 255, mz = (mm >> 16) & 255, tm = mm >> 24;
+        for (int ks = 0; ks < G.KS; ks++) {
+          if (!bad && j == 0) {
+            if (!mbar_wait(full0 + 8 * slot, phase, abort_flag)) {
+              if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+              *abort_flag = 1;
+              bad = true;
+            }
+            tc_fence_after();
+            sa = ring0 + slot * R.slot_bytes;
+            kb0 = sa + R.kps * G.a_bytes - G.ks_off[ks];
+          }
+          if (!bad) {
+            const uint32_t as = sa + j * G.a_bytes;
+            const uint64_t ad = sdesc(as);
 #pragma unroll
-              for (int u = 0; u < E; u++) {
-                const int n = E * q + u;
-                if (n < nc) {
-                  const int nn = mi[n], tn = nn >> 24;
-                  if (tn + tm <= p)
-                    v[u] = bk[idx3((nn & 255) + ma, ((nn >> 8) & 255) + mb, ((nn >> 16) & 255) + mz)] * fp[tn];
+            for (int g = 0; g < TC_MAXG; g++) {
+              if (g < G.na[ks]) {
+                const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, G.N[g]);
+                const uint32_t kg = kb0 + G.ks_off[ks] + G.ncopy * 32 * G.rowpre[g];
+                const uint64_t bd = sdesc(kg);
+                mma<BF16>(tmem + G.col[g], ad, bd, id, ks == 0 ? acc : 1u);
+                if constexpr (BF16) {
+                  mma<BF16>(tmem + G.col[g], ad, sdesc(kg + 32 * G.N[g]), id, 1u);  // hi x lo
+                  mma<BF16>(tmem + G.col[g], sdesc(as + TC_SLICE), bd, id, 1u);     // lo x hi
                 }
               }
             }
-            const int off = tile_off<BF16>(r, E * q, G.sbo[g]);
-            store_row<BF16>(tile + off, tile + G.b_bytes + off, v);
-          }
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a_hi = smem_u32(As), b_hi = smem_u32(Bs);
-        for (int g = 0; g < G.ng; g++) {
-          const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, G.N[g]);
-          for (int ks = 0; ks < G.K[g] / (2 * E); ks++) {  // one k-step = 32 bytes of K = 2 core matrices
-            const uint32_t ao = ks * 256, bo = G.boff[g] + ks * 256;
-            const uint64_t ad = smem_desc(a_hi + ao, 128, G.sbo_a);
-            const uint64_t bd = smem_desc(b_hi + bo, 128, G.sbo[g]);
-            const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-            mma<BF16>(tmem + G.col[g], ad, bd, id, acc);
-            if constexpr (BF16) {
-              const uint64_t adl = smem_desc(a_hi + G.a_bytes + ao, 128, G.sbo_a);
-              const uint64_t bdl = smem_desc(b_hi + G.b_bytes + bo, 128, G.sbo[g]);
-              mma<BF16>(tmem + G.col[g], ad, bdl, id, 1u);  // hi x lo
-              mma<BF16>(tmem + G.col[g], adl, bd, id, 1u);  // lo x hi
+            if (++j == R.kps || ks == G.KS - 1) {
+              mma_commit(empty0 + 8 * slot);  // the slot is free once these MMAs have read it
+              n++;
+              j = 0;
+              if (++slot == R.nslots) {
+                slot = 0;
+                phase ^= 1u;
+              }
             }
           }
         }
-        mma_commit(bar);
+        acc = 1u;
       }
-      first = false;
-      // the operands may be overwritten once the tensor core has read them
-      const bool ok = mbar_wait(bar, phase);
-      if (!ok) {
-        if (tid == 0) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
-        mbar_wait(bar, phase);  // once more, bounded, for the MMAs in flight
-        *abort_flag = 1;
-      }
-      phase ^= 1;
-      tc_fence_after();
-      __syncthreads();
-      if (*abort_flag) break;
+      counts[1] = n;
+      mma_commit(smem_u32(done));  // arrives when every MMA issued above has completed
     }
-    if (*abort_flag) break;
-  }
-  // ---- epilogue: warps 0-3 read lanes 32w .. 32w+31 (states) of every group
-  if (!*abort_flag && warp < 4 && !first) {
-    const float inv = (float)(1.0 / (4.0 * M_PI * sT));
-    const int b = b0 + warp * 32 + lane;
-    for (int g = 0; g < G.ng; g++) {
-      for (int c0 = 0; c0 < G.N[g]; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(G.col[g] + c0), r);
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ---- epilogue: warp 4 + q reads TMEM lanes 32q .. 32q + 31 (states)
+    const int q = warp - 4;
+    const bool ok = mbar_wait(smem_u32(done), 0, nullptr);
+    if (!ok) {
+      atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+      *abort_flag = 1;
+      mbar_wait(smem_u32(done), 0, nullptr);  // once more, bounded, for the MMAs in flight
+    }
+    tc_fence_after();
+    if (ok && !*abort_flag) {
+      const float inv = (float)(1.0 / (4.0 * M_PI * ldexp(side, -level[T])));
+      const int b = sb * TC_M + q * 32 + lane;
+      float* Lt = L + (int64_t)T * nc * B + b;
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
-          const int row = c0 + i;
-          if (row < G.nrow[g] && b < B) {
-            const int m = G.m0[g] + row;
-            const float sg = ((mi[m] >> 24) & 1) ? -inv : inv;
-            L[((int64_t)T * nc + m) * B + b] = sg * __uint_as_float(r[i]);
+      for (int g = 0; g < G.ng; g++) {
+#pragma unroll
+        for (int c0 = 0; c0 < G.N[g]; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(G.col[g] + c0), r);
+          if (b < B) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              const int m = G.m0[g] + c0 + i;
+              if (c0 + i < G.nrow[g]) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
+            }
           }
         }
       }
     }
   }
+  __syncthreads();
+  if (tid == 0 && *abort_flag) {
+    // copies issued but never consumed still land in the ring: wait for them
+    for (int it = counts[1]; it < counts[0]; it++)
+      mbar_wait(full0 + 8 * (it % R.nslots), (uint32_t)((it / R.nslots) & 1), nullptr);
+  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
+  if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_cols) : "memory");
 }
 
-// level groups for order p: minimise the padded tile area sum N_g * K_g
-// (epr = elements per 16 bytes: K is padded to one k-step of 2 * epr)
-bool make_groups(int p, int epr, TcGroups& G) {
-  auto cnc = [](int t) { return t < 0 ? 0 : (t + 1) * (t + 2) * (t + 3) / 6; };
-  auto pad = [](int x, int m) { return (x + m - 1) / m * m; };
-  const int T = p + 1, kstep = 2 * epr;
-  std::vector<long> best(T + 1, -1);
-  std::vector<int> from(T + 1, -1);
-  best[0] = 0;
-  for (int tb = 1; tb <= T; tb++)  // groups cover degrees [ta, tb)
-    for (int ta = 0; ta < tb; ta++) {
-      if (best[ta] < 0) continue;
-      const long cost = (long)pad(cnc(tb - 1) - cnc(ta - 1), 16) * pad(cnc(p - ta), kstep) + 256;
-      if (best[tb] < 0 || best[ta] + cost < best[tb]) {
-        best[tb] = best[ta] + cost;
-        from[tb] = ta;
-      }
-    }
-  std::vector<std::pair<int, int>> gs;
-  for (int tb = T; tb > 0; tb = from[tb]) gs.push_back({from[tb], tb});
-  std::reverse(gs.begin(), gs.end());
-  if ((int)gs.size() > TC_MAXG) return false;
-  G.ng = (int)gs.size();
-  int col = 0, boff = 0;
-  G.kmax = 0;
-  for (int g = 0; g < G.ng; g++) {
-    const int ta = gs[g].first, tb = gs[g].second;
-    G.m0[g] = cnc(ta - 1);
-    G.nrow[g] = cnc(tb - 1) - cnc(ta - 1);
-    G.N[g] = pad(G.nrow[g], 16);
-    G.K[g] = pad(cnc(p - ta), kstep);
-    G.col[g] = col;
-    col += G.N[g];
-    G.sbo[g] = (G.K[g] / epr) * 128 + 16;  // +16 bytes spreads the 8-row groups over the banks
-    G.boff[g] = boff;
-    boff = pad(boff + (G.N[g] / 8) * G.sbo[g], 128);
-    G.kmax = std::max(G.kmax, G.K[g]);
-  }
-  G.sbo_a = (G.kmax / epr) * 128 + 16;
-  G.a_bytes = pad((TC_M / 8) * G.sbo_a, 1024);
-  G.b_bytes = pad(boff, 128);
-  int tc = 32;
-  while (tc < col) tc *= 2;
-  if (tc > 512) return false;
-  G.tmem_cols = tc;
-  return true;
+// ---------------------------------------------------------------------------
+// host side
+void cell_coords(uint64_t prefix, int level, int64_t* k) {  // integer box coordinates (x bit at 3b)
+  k[0] = k[1] = k[2] = 0;
+  for (int b = 0; b < level; b++)
+    for (int a = 0; a < 3; a++) k[a] |= (int64_t)((prefix >> (3 * b + a)) & 1ull) << b;
 }
 
-size_t tc_smem_bytes(const TcGroups& G, int nc, int ncopy) {
-  return (size_t)ncopy * (G.a_bytes + G.b_bytes) + sizeof(float) * (TC_BCH * nc + TC_BCH * 16 + TC_BCH * 4) +
-         sizeof(int) * ((nc + 1) & ~1) + sizeof(uint64_t) + 2 * sizeof(uint32_t) + 64;
+struct KeyHash {
+  size_t operator()(const std::array<int64_t, 4>& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t v : k) h = (h ^ (uint64_t)v) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+
+TcLayout layout_of(const Plan& P) { return tc_layout(P.p, P.opt.precision == DEMAG_MIXED_BF16X3); }
+
+template <int PP, bool BF16>
+void launch_fixed(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
+  static size_t attr = 0;
+  const size_t smem = ring_smem(R);
+  if (smem > attr) {
+    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const int nsb = (B + TC_M - 1) / TC_M;
+  dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)nsb);
+  k_m2l_tc<PP, BF16><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.m2l_op, P.cell_level,
+                                                    P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+  DM_LAUNCH("k_m2l_tc");
 }
 
 template <bool BF16>
-bool launch(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s) {
-  TcGroups G;
-  if (!make_groups(P.p, EPR<BF16>, G)) return false;
-  const size_t smem = tc_smem_bytes(G, P.nc, BF16 ? 2 : 1);
-  if (smem > 227 * 1024) return false;
-  static size_t attr = 0;
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
+void launch_order(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
+  switch (P.p) {
+    case 4: launch_fixed<4, BF16>(P, R, B, QP, L, err, s); break;
+    case 6: launch_fixed<6, BF16>(P, R, B, QP, L, err, s); break;
+    case 8: launch_fixed<8, BF16>(P, R, B, QP, L, err, s); break;
+    case 10: launch_fixed<10, BF16>(P, R, B, QP, L, err, s); break;
+    default: fail(DEMAG_ERR_UNSUPPORTED, "no tensor-core M2L for this order");
   }
-  dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((B + TC_M - 1) / TC_M));
-  k_m2l_tc<BF16><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre, P.cell_level,
-                                                P.side, P.p, P.nc, B, G, Q, L, err);
-  DM_LAUNCH("k_m2l_tc");
-  return true;
+}
+
+void launch_main(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
+  if (P.opt.precision == DEMAG_MIXED_BF16X3)
+    launch_order<true>(P, R, B, QP, L, err, s);
+  else
+    launch_order<false>(P, R, B, QP, L, err, s);
+}
+
+// ring budgets: ~100 KB lets two CTAs share an SM (when their tensor memory
+// fits), ~200 KB gives one CTA the whole shared memory
+constexpr int TC_BUDGET_2 = 100 * 1024, TC_BUDGET_1 = 200 * 1024;
+
+// default ring shape: two CTAs per SM, ~32 KB slots
+void default_ring(const TcLayout& G, TcRing& R) {
+  const int budget = G.tmem_cols <= 256 ? TC_BUDGET_2 : TC_BUDGET_1;
+  int kps = std::max(1, std::min(G.KS, (32 * 1024) / G.a_bytes / 2));
+  while (kps > 1 && !make_ring(G, kps, budget, R)) kps--;
+  if (!make_ring(G, kps, budget, R)) make_ring(G, 1, TC_BUDGET_1, R);
+}
+
+// autotune: time every ring shape on the plan's own lists (zero moments,
+// 128 states) and keep the fastest
+void tune_ring(Plan& P, const TcLayout& G) {
+  cudaStream_t s = P.stream;
+  const int B = TC_M;
+  Tmp<unsigned char> qp((size_t)P.ncells * G.KS * G.a_bytes);
+  Tmp<float> L((size_t)P.ncells * P.nc * B);
+  Tmp<int> err(1);
+  DM_CUDA(cudaMemsetAsync(qp.p, 0, (size_t)P.ncells * G.KS * G.a_bytes, s));
+  DM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  cudaEvent_t a, b;
+  DM_CUDA(cudaEventCreate(&a));
+  DM_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int budget : {TC_BUDGET_2, TC_BUDGET_1}) {
+    if (budget == TC_BUDGET_2 && G.tmem_cols > 256) continue;
+    for (int kps = 1; kps <= std::min(G.KS, 8); kps++) {
+      TcRing R;
+      if (!make_ring(G, kps, budget, R)) continue;
+      if (R.nslots < 2 || ring_smem(R) > 227 * 1024) continue;
+      launch_main(P, R, B, qp.p, L.p, err.p, s);  // warm-up
+      DM_CUDA(cudaEventRecord(a, s));
+      launch_main(P, R, B, qp.p, L.p, err.p, s);
+      DM_CUDA(cudaEventRecord(b, s));
+      DM_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      DM_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best) {
+        best = ms;
+        P.tc_kps = kps;
+        P.tc_budget = budget;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  int h_err = 0;
+  DM_CUDA(cudaMemcpy(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_err) fail(DEMAG_ERR_TIMEOUT, "tensor-core M2L timed out while tuning");
+}
+
+bool current_ring(const Plan& P, const TcLayout& G, TcRing& R) {
+  if (P.tc_kps > 0 && make_ring(G, P.tc_kps, P.tc_budget, R)) return true;
+  default_ring(G, R);
+  return R.nslots >= 2;
+}
+
+template <bool BF16>
+void build_ops(Plan& P, const TcLayout& G, const std::vector<int4>& keys) {
+  cudaStream_t s = P.stream;
+  P.tc_ops = dalloc<unsigned char>(P, (size_t)keys.size() * G.op_bytes);
+  Tmp<int4> dkeys(keys.size());
+  DM_CUDA(cudaMemcpyAsync(dkeys.p, keys.data(), keys.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  k_m2l_tc_ops<BF16><<<(unsigned)keys.size(), 128, 0, s>>>(dkeys.p, P.p, P.nc, G, P.tc_ops);
+  DM_LAUNCH("k_m2l_tc_ops");
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
+bool tc_enabled(const Plan& P) {
+  return (P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3) && P.tc_ops != nullptr;
 }
 
 }  // namespace
 
-bool launch_m2l_tc(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s) {
+void build_m2l_tc(Plan& P) {
+  if (P.opt.precision != DEMAG_MIXED_TF32 && P.opt.precision != DEMAG_MIXED_BF16X3) return;
+  if (P.n_m2l == 0 || !tc_order(P.p)) return;  // the CUDA-core M2L runs instead
+  const TcLayout G = layout_of(P);
+  if (!G.valid) return;
+  cudaStream_t s = P.stream;
+  const int64_t nc = P.ncells;
+  std::vector<uint64_t> prefix(nc);
+  std::vector<int32_t> lev(nc), src(P.n_m2l);
+  std::vector<int64_t> off(nc + 1);
+  DM_CUDA(cudaMemcpyAsync(prefix.data(), P.cell_prefix, nc * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(lev.data(), P.cell_level, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(off.data(), P.m2l_off, (nc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(src.data(), P.m2l_src, P.n_m2l * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  std::vector<std::array<int64_t, 3>> kc(nc);
+  for (int64_t c = 0; c < nc; c++) cell_coords(prefix[c], lev[c], kc[c].data());
+  std::unordered_map<std::array<int64_t, 4>, int32_t, KeyHash> index;
+  std::vector<int4> keys;
+  std::vector<int32_t> op(P.n_m2l);
+  for (int64_t T = 0; T < nc; T++)
+    for (int64_t e = off[T]; e < off[T + 1]; e++) {
+      const int32_t S = src[e];
+      const int dl = lev[T] - lev[S];
+      std::array<int64_t, 4> key{dl, 0, 0, 0};
+      for (int a = 0; a < 3; a++)
+        key[1 + a] = dl >= 0 ? (2 * kc[T][a] + 1) - ((2 * kc[S][a] + 1) << dl)
+                             : ((2 * kc[T][a] + 1) << (-dl)) - (2 * kc[S][a] + 1);
+      auto f = index.find(key);
+      if (f == index.end()) {
+        for (int a = 1; a < 4; a++)
+          if (key[a] > INT32_MAX || key[a] < INT32_MIN) return;  // beyond the table's key range
+        f = index.emplace(key, (int32_t)keys.size()).first;
+        keys.push_back(make_int4(dl, (int)key[1], (int)key[2], (int)key[3]));
+      }
+      op[e] = f->second;
+    }
+  P.m2l_op = dalloc<int32_t>(P, P.n_m2l);
+  DM_CUDA(cudaMemcpyAsync(P.m2l_op, op.data(), P.n_m2l * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  P.n_tc_ops = (int64_t)keys.size();
+  if (G.bf16)
+    build_ops<true>(P, G, keys);
+  else
+    build_ops<false>(P, G, keys);
+  P.tc_kps = 0;
+  P.tc_budget = 0;
+  if (P.opt.autotune) tune_ring(P, G);
+  TcRing R;
+  if (!current_ring(P, G, R)) fail(DEMAG_ERR_UNSUPPORTED, "no ring shape fits the tensor-core M2L");
+  P.tc_kps = R.kps;
+  P.tc_budget = R.nslots * R.slot_bytes;
+}
+
+size_t m2l_tc_pack_bytes(const Plan& P, int B) {
+  if (!tc_enabled(P)) return 0;
+  const TcLayout G = layout_of(P);
+  const size_t nsb = (size_t)(B + TC_M - 1) / TC_M;
+  return (size_t)P.ncells * nsb * G.KS * G.a_bytes;
+}
+
+bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, int* err, cudaStream_t s) {
   if (P.h_m2l_targets.empty()) return true;
-  if (P.opt.precision == DEMAG_MIXED_BF16X3) return launch<true>(P, B, Q, L, err, s);
-  return launch<false>(P, B, Q, L, err, s);
+  if (!tc_enabled(P) || QP == nullptr) return false;
+  const TcLayout G = layout_of(P);
+  TcRing R;
+  if (!current_ring(P, G, R)) return false;
+  const int nsb = (B + TC_M - 1) / TC_M;
+  if (G.bf16)
+    k_m2l_tc_pack<true><<<dim3((unsigned)P.ncells, (unsigned)nsb), TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, QP);
+  else
+    k_m2l_tc_pack<false><<<dim3((unsigned)P.ncells, (unsigned)nsb), TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, QP);
+  DM_LAUNCH("k_m2l_tc_pack");
+  launch_main(P, R, B, QP, L, err, s);
+  return true;
 }
 
 }  // namespace demag

@@ -78,6 +78,8 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     w.Q32 = c.take<float>(ncell * nc * B + 16);  // tail pad for 16-byte bulk copies
     w.L32 = c.take<float>(ncell * nc * B);
     w.u32 = c.take<float>(nn * B);
+    const size_t qp = m2l_tc_pack_bytes(P, B);
+    if (qp) w.QP = c.take<unsigned char>(qp);
   }
   w.u_s = c.take<double>(nn * B);
   if (otf) w.state = c.take<double>(nt * TET_STATE * B);
@@ -91,6 +93,7 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     W->Q32 = w.Q32;
     W->L32 = w.L32;
     W->u32 = w.u32;
+    W->QP = w.QP;
     W->u_s = w.u_s;
     W->state = w.state;
     W->err = w.err;

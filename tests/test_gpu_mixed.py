@@ -135,3 +135,18 @@ def test_bench_workload_mixed_vs_fp64_and_oracle_sample(orc):
     ref = tr.fmm(M[0], 8, target_leaves=pick)
     sel = np.concatenate([ex["node_perm"][ex["cell_ranges"][c, 2]:ex["cell_ranges"][c, 3]] for c in pick])
     assert rel_l2(u64[0].cpu().numpy()[sel], ref[sel]) < 1e-10
+
+
+def test_tensor_core_ring_shape_does_not_change_results():
+    """The autotuner only picks the shared-memory ring shape of the
+    tensor-core M2L; the MMA sequence, and so every bit of the result, is the
+    same for every shape."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=128)
+    a = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1, precision="bf16x3")
+    b = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1, precision="bf16x3", autotune=True)
+    sa, sb = a.stats(), b.stats()
+    assert sa["n_m2l_ops"] > 0 and sa["m2l_kps"] > 0 and sb["m2l_kps"] > 0
+    ua, Ha = a.eval(M)
+    ub, Hb = b.eval(M)
+    assert torch.equal(ua, ub) and torch.equal(Ha, Hb)
