@@ -32,6 +32,15 @@ constexpr int MAX_NCOEF = (MAX_P + 1) * (MAX_P + 2) * (MAX_P + 3) / 6;  // 455
 
 __host__ __device__ inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
+// one coefficient of an FP32 octree translation: target coefficient += (bit
+// `octant` of neg ? -c : c) * source coefficient k (octant of the child cell)
+struct TEnt {
+  uint16_t k;
+  uint8_t neg;
+  uint8_t pad;
+  float c;
+};
+
 // Graded multi-index order: total degree t ascending; within t, n_x descending,
 // then n_z ascending.  Index of (a,b,c):
 //   t(t+1)(t+2)/6 + (b+c)(b+c+1)/2 + c,  t = a+b+c.
@@ -161,6 +170,20 @@ struct Plan {
   unsigned char* tc_ops = nullptr;
   int32_t* m2l_op = nullptr;        // n_m2l
   int tc_kps = 0, tc_budget = 0;    // ring shape of the M2L kernel: k-steps per slot, ring bytes
+
+  // FP32 octree translations as coefficient lists (mixed precision):
+  //   M2M: Qt^P_n += sum over entries e of n: sign_e(octant) c_e Qt^C_{k_e}
+  //   L2L: Lt^C_m += sum over entries e of m: sign_e(octant) c_e Lt^P_{k_e}
+  int32_t* m2m_eoff = nullptr;      // nc + 1
+  TEnt* m2m_ent = nullptr;
+  int32_t* l2l_eoff = nullptr;      // nc + 1
+  TEnt* l2l_ent = nullptr;
+  // FP32 mass-lumped gradient operator (mixed precision), rows by sorted node:
+  //   H_i = sum_e w_e u_{col_e},  w_e = -(1/V_i) sum_{t ni i, col_e} vol_t grad lambda_{col_e}^t
+  int64_t* hg_off = nullptr;        // nn + 1
+  int32_t* hg_col = nullptr;
+  float4* hg_w = nullptr;           // (x, y, z, 0)
+  int32_t* node_iperm = nullptr;    // original -> sorted node
 
   // FP32 far-field operators (mixed precision, per-level scaled)
   float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)  float* cell_side32 = nullptr;     // per cell side length (float)

@@ -15,6 +15,10 @@
 // FP64 coefficient set W rounded to FP32 (near.cu), or the FP64 on-the-fly
 // P2P when near_mode = 0.  u is accumulated in FP32 and the mass-lumped H is
 // formed in FP64 from it.
+#include <algorithm>
+#include <array>
+#include <cmath>
+
 #include "common.cuh"
 
 namespace demag {
@@ -30,19 +34,6 @@ __device__ __forceinline__ void load_mi(int nc, unsigned char (*mi)[3]) {
     mi[i][0] = (unsigned char)a;
     mi[i][1] = (unsigned char)b;
     mi[i][2] = (unsigned char)c;
-  }
-}
-
-// s_j(d) for |j| <= p; d is one of (+-h, +-h, +-h) given by the octant bits
-__device__ __forceinline__ void octant_monomials(int p, int nc, const unsigned char (*mi)[3], int octant, float h,
-                                                 float* s) {
-  const float dx = (octant & 1) ? h : -h, dy = (octant & 2) ? h : -h, dz = (octant & 4) ? h : -h;
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-    float v = 1.f;
-    for (int e = 1; e <= mi[j][0]; e++) v = v * dx / e;
-    for (int e = 1; e <= mi[j][1]; e++) v = v * dy / e;
-    for (int e = 1; e <= mi[j][2]; e++) v = v * dz / e;
-    s[j] = v;
   }
 }
 
@@ -72,58 +63,82 @@ __global__ void k_ghat32(const int32_t* __restrict__ leaves, const int32_t* __re
     }
 }
 
-__global__ void k_p2m32(const int32_t* __restrict__ leaves, const int64_t* __restrict__ sup_off,
-                        const int32_t* __restrict__ sup_node, const float* __restrict__ G, const float* __restrict__ Ms,
-                        int nc, int nc1, int B, float* Q) {
-  __shared__ unsigned char mi[MAX_NCOEF][3];
-  load_mi(nc, mi);
-  __syncthreads();
+// P2M: one block per (source leaf, 8 coefficients n, 128 states); the leaf's
+// Gt rows are staged in shared memory 16 support nodes at a time, with a zero
+// entry at index nc1 standing for "no such coefficient" (n_c = 0)
+constexpr int P2M_NN = 8, P2M_NE = 16, P2M_B = 128;
+
+__global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ leaves,
+                                                 const int64_t* __restrict__ sup_off,
+                                                 const int32_t* __restrict__ sup_node, const float* __restrict__ G,
+                                                 const float* __restrict__ Ms, int nc, int nc1, int B, float* Q) {
+  __shared__ float sG[P2M_NE][MAX_NCOEF + 1];
   const int32_t c = leaves[blockIdx.x];
-  const int64_t so = sup_off[c], eo = sup_off[c + 1];
-  for (int idx = threadIdx.x; idx < nc * B; idx += blockDim.x) {
-    const int n = idx / B, b = idx - n * B;
-    const int na = mi[n][0], nb = mi[n][1], nz = mi[n][2];
-    const int ix = na ? mi_index(na - 1, nb, nz) : -1;
-    const int iy = nb ? mi_index(na, nb - 1, nz) : -1;
-    const int iz = nz ? mi_index(na, nb, nz - 1) : -1;
-    float acc = 0;
-    for (int64_t e = so; e < eo; e++) {
-      const float* g = G + e * nc1;
-      const float* m = Ms + (int64_t)sup_node[e] * 3 * B + b;
-      if (ix >= 0) acc += g[ix] * m[0];
-      if (iy >= 0) acc += g[iy] * m[B];
-      if (iz >= 0) acc += g[iz] * m[2 * B];
-    }
-    Q[((int64_t)c * nc + n) * B + b] = acc;
+  const int n0 = blockIdx.y * P2M_NN;
+  const int b = blockIdx.z * P2M_B + threadIdx.x;
+  const bool live = b < B;
+  int ix[P2M_NN][3];
+#pragma unroll
+  for (int j = 0; j < P2M_NN; j++) {
+    int na = 0, nb = 0, nz = 0;
+    const bool ok = n0 + j < nc;
+    if (ok) mi_decode(n0 + j, na, nb, nz);
+    ix[j][0] = (ok && na) ? mi_index(na - 1, nb, nz) : nc1;
+    ix[j][1] = (ok && nb) ? mi_index(na, nb - 1, nz) : nc1;
+    ix[j][2] = (ok && nz) ? mi_index(na, nb, nz - 1) : nc1;
   }
+  float acc[P2M_NN];
+#pragma unroll
+  for (int j = 0; j < P2M_NN; j++) acc[j] = 0.f;
+  const int64_t so = sup_off[c], eo = sup_off[c + 1];
+  for (int64_t e0 = so; e0 < eo; e0 += P2M_NE) {
+    const int ne = (int)min((int64_t)P2M_NE, eo - e0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < ne * (nc1 + 1); q += blockDim.x) {
+      const int r = q / (nc1 + 1), m = q - r * (nc1 + 1);
+      sG[r][m] = m < nc1 ? G[(e0 + r) * nc1 + m] : 0.f;
+    }
+    __syncthreads();
+    if (live) {
+      for (int r = 0; r < ne; r++) {
+        const float* mp = Ms + (int64_t)sup_node[e0 + r] * 3 * B + b;
+        const float m0 = mp[0], m1 = mp[B], m2 = mp[2 * B];
+#pragma unroll
+        for (int j = 0; j < P2M_NN; j++) acc[j] += sG[r][ix[j][0]] * m0 + sG[r][ix[j][1]] * m1 + sG[r][ix[j][2]] * m2;
+      }
+    }
+  }
+  if (live)
+#pragma unroll
+    for (int j = 0; j < P2M_NN; j++)
+      if (n0 + j < nc) Q[((int64_t)c * nc + n0 + j) * B + b] = acc[j];
 }
 
-__global__ void k_m2m32(int64_t lb, const int32_t* __restrict__ child0, const int32_t* __restrict__ nchild,
-                        const uint64_t* __restrict__ prefix, int p, int nc, int B, float* Q) {
-  __shared__ unsigned char mi[MAX_NCOEF][3];
-  __shared__ float s[8][MAX_NCOEF];
-  const int64_t P = lb + blockIdx.x;
-  const int n_ch = nchild[P];
-  if (n_ch == 0) return;
-  load_mi(nc, mi);
-  __syncthreads();
+// M2M of one level: thread per (cell, n, state); the warp shares (cell, n), so
+// the coefficient list is read as a broadcast and the child moments coalesce
+__global__ void k_m2m32(int64_t lb, int64_t ncl, const int32_t* __restrict__ child0, const int32_t* __restrict__ nchild,
+                        const uint64_t* __restrict__ prefix, const int32_t* __restrict__ eoff,
+                        const TEnt* __restrict__ ent, int nc, int B, float* Q) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)nc * B;
+  if (idx >= ncl * per) return;
+  const int64_t P = lb + idx / per;
+  const int rem = (int)(idx % per), n = rem / B, b = rem - n * B;
+  const int nch = nchild[P];
+  if (nch == 0) return;
   const int32_t c0 = child0[P];
-  for (int k = 0; k < n_ch; k++) octant_monomials(p, nc, mi, (int)(prefix[c0 + k] & 7ull), 0.25f, s[k]);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nc * B; idx += blockDim.x) {
-    const int n = idx / B, b = idx - n * B;
-    const int na = mi[n][0], nb = mi[n][1], nz = mi[n][2];
-    float acc = 0;
-    for (int k = 0; k < n_ch; k++) {
-      const float* Qc = Q + (int64_t)(c0 + k) * nc * B + b;
-      for (int ka = 0; ka <= na; ka++)
-        for (int kb = 0; kb <= nb; kb++)
-          for (int kz = 0; kz <= nz; kz++)
-            acc += s[k][mi_index(na - ka, nb - kb, nz - kz)] * ldexpf(Qc[(int64_t)mi_index(ka, kb, kz) * B],
-                                                                    -(ka + kb + kz));
+  const int e0 = eoff[n], e1 = eoff[n + 1];
+  float acc = 0.f;
+  for (int k = 0; k < nch; k++) {
+    const int oct = (int)(prefix[c0 + k] & 7ull);
+    const float* Qc = Q + (int64_t)(c0 + k) * per + b;
+    for (int e = e0; e < e1; e++) {
+      const TEnt E = ent[e];
+      const float v = Qc[(int64_t)E.k * B];
+      acc = fmaf(((E.neg >> oct) & 1) ? -E.c : E.c, v, acc);
     }
-    Q[(P * nc + n) * B + b] = acc;
   }
+  Q[P * per + (int64_t)n * B + b] = acc;
 }
 
 // CUDA-core M2L: one block per target cell, threads over (m, state)
@@ -197,40 +212,36 @@ __global__ void k_m2l32(const int32_t* __restrict__ targets, const int64_t* __re
   }
 }
 
-__global__ void k_l2l32(int64_t lb, const int32_t* __restrict__ parent, const int4* __restrict__ range,
-                        const uint64_t* __restrict__ prefix, int p, int nc, int B, float* L) {
-  __shared__ unsigned char mi[MAX_NCOEF][3];
-  __shared__ float s[MAX_NCOEF];
-  const int64_t C = lb + blockIdx.x;
+// L2L of one level: thread per (child cell, m, state), added to the child's
+// own M2L result
+__global__ void k_l2l32(int64_t lb, int64_t ncl, const int32_t* __restrict__ parent, const int4* __restrict__ range,
+                        const uint64_t* __restrict__ prefix, const int32_t* __restrict__ eoff,
+                        const TEnt* __restrict__ ent, int nc, int B, float* L) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)nc * B;
+  if (idx >= ncl * per) return;
+  const int64_t C = lb + idx / per;
   const int4 r = range[C];
-  if (r.w == r.z) return;
-  const int32_t P = parent[C];
-  load_mi(nc, mi);
-  __syncthreads();
-  octant_monomials(p, nc, mi, (int)(prefix[C] & 7ull), 0.5f, s);
-  __syncthreads();
-  const float* Lp = L + (int64_t)P * nc * B;
-  for (int idx = threadIdx.x; idx < nc * B; idx += blockDim.x) {
-    const int m = idx / B, b = idx - m * B;
-    const int ma = mi[m][0], mb = mi[m][1], mz = mi[m][2];
-    const int tm = ma + mb + mz;
-    float acc = 0;
-    int j = 0;
-    for (int t = 0; t <= p - tm; t++)
-      for (int jj = 0; jj <= t; jj++)
-        for (int jz = 0; jz <= jj; jz++, j++) {
-          const int ja = t - jj, jb = jj - jz;
-          acc += s[j] * ldexpf(Lp[(int64_t)mi_index(ma + ja, mb + jb, mz + jz) * B + b], -(tm + t));
-        }
-    L[((int64_t)C * nc + m) * B + b] += acc;
+  if (r.w == r.z) return;  // no target nodes below this cell
+  const int rem = (int)(idx % per), m = rem / B, b = rem - m * B;
+  const int oct = (int)(prefix[C] & 7ull);
+  const float* Lp = L + (int64_t)parent[C] * per + b;
+  float acc = 0.f;
+  for (int e = eoff[m], e1 = eoff[m + 1]; e < e1; e++) {
+    const TEnt E = ent[e];
+    acc = fmaf(((E.neg >> oct) & 1) ? -E.c : E.c, Lp[(int64_t)E.k * B], acc);
   }
+  L[C * per + (int64_t)m * B + b] += acc;
 }
 
+// L2P: thread per (node, state); u = sum_m Lt_m s_m(z/s) over the node's leaf
 __global__ void k_l2p32(int64_t nn, const int32_t* __restrict__ node_leaf, const int32_t* __restrict__ level,
                         const double* __restrict__ nodes_s, const double* __restrict__ centre, double side, int p,
                         int nc, int B, const float* __restrict__ L, float* u) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nn) return;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nn * B) return;
+  const int64_t i = idx / B;
+  const int b = (int)(idx - i * B);
   const int32_t c = node_leaf[i];
   const double inv_s = 1.0 / ldexp(side, -level[c]);
   float px[MAX_P + 1], py[MAX_P + 1], pz[MAX_P + 1];
@@ -238,20 +249,69 @@ __global__ void k_l2p32(int64_t nn, const int32_t* __restrict__ node_leaf, const
               zy = (float)((nodes_s[3 * i + 1] - centre[3 * c + 1]) * inv_s),
               zz = (float)((nodes_s[3 * i + 2] - centre[3 * c + 2]) * inv_s);
   px[0] = py[0] = pz[0] = 1.f;
-  for (int e = 1; e <= p; e++) {
+#pragma unroll
+  for (int e = 1; e <= MAX_P; e++) {
     px[e] = px[e - 1] * zx / e;
     py[e] = py[e - 1] * zy / e;
     pz[e] = pz[e - 1] * zz / e;
   }
-  const float* Lc = L + (int64_t)c * nc * B;
-  for (int b = 0; b < B; b++) {
-    float v = 0;
-    int m = 0;
-    for (int t = 0; t <= p; t++)
-      for (int j = 0; j <= t; j++)
-        for (int mz = 0; mz <= j; mz++, m++) v += Lc[(int64_t)m * B + b] * px[t - j] * py[j - mz] * pz[mz];
-    u[i * B + b] = v;
+  const float* Lc = L + (int64_t)c * nc * B + b;
+  float v = 0.f;
+  int m = 0;
+#pragma unroll
+  for (int t = 0; t <= MAX_P; t++) {
+    if (t > p) break;
+#pragma unroll
+    for (int j = 0; j <= t; j++)
+#pragma unroll
+      for (int mz = 0; mz <= j; mz++, m++) v = fmaf(Lc[(int64_t)m * B], px[t - j] * py[j - mz] * pz[mz], v);
   }
+  u[i * B + b] = v;
+}
+
+// u and the mass-lumped H of the mixed path, in the caller's layout: tiles of
+// 32 original nodes x 32 states; reads coalesce over states, the transposed
+// tile is written coalesced over nodes
+__global__ void __launch_bounds__(256) k_out32(int64_t nn, int B, const int32_t* __restrict__ iperm,
+                                               const int64_t* __restrict__ hoff, const int32_t* __restrict__ hcol,
+                                               const float4* __restrict__ hw, const float* __restrict__ u32,
+                                               double* u_out, double* H_out) {
+  __shared__ float su[32][33];
+  __shared__ float sh[32][97];
+  const int64_t g0 = (int64_t)blockIdx.x * 32;
+  const int b0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = b0 + lane;
+  for (int r = w; r < 32; r += 8) {
+    const int64_t g = g0 + r;
+    float uu = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+    if (g < nn && b < B) {
+      const int64_t i = iperm[g];
+      uu = u32[i * B + b];
+      if (H_out)
+        for (int64_t e = hoff[i], e1 = hoff[i + 1]; e < e1; e++) {
+          const float4 wv = hw[e];
+          const float uj = u32[(int64_t)hcol[e] * B + b];
+          hx = fmaf(wv.x, uj, hx);
+          hy = fmaf(wv.y, uj, hy);
+          hz = fmaf(wv.z, uj, hz);
+        }
+    }
+    su[lane][r] = uu;
+    sh[lane][3 * r] = hx;
+    sh[lane][3 * r + 1] = hy;
+    sh[lane][3 * r + 2] = hz;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int bl = q >> 5, gl = q & 31;
+    if (b0 + bl < B && g0 + gl < nn) u_out[(int64_t)(b0 + bl) * nn + g0 + gl] = (double)su[bl][gl];
+  }
+  if (H_out)
+    for (int q = threadIdx.x; q < 32 * 96; q += blockDim.x) {
+      const int bl = q / 96, rr = q - bl * 96;
+      if (b0 + bl < B && g0 + rr / 3 < nn) H_out[((int64_t)(b0 + bl) * nn + g0) * 3 + rr] = (double)sh[bl][rr];
+    }
 }
 
 __global__ void k_u32_to_64(int64_t n, const float* __restrict__ a, double* b) {
@@ -261,7 +321,124 @@ __global__ void k_u32_to_64(int64_t n, const float* __restrict__ a, double* b) {
 
 }  // namespace
 
+// coefficient lists of the FP32 translations (see the file header):
+//   M2M  n <- k <= n,  j = n - k:  c = s_j(1/4) 2^-|k|, child centre - parent centre = +-s_P/4
+//   L2L  m <- k = m + j, |k| <= p:  c = s_j(1/2) 2^-|k|, child centre - parent centre = +-s_C/2
+// with the sign of s_j(d) for the child octant o: d_i = +h if bit i of o is set, else -h
+static void build_translations(Plan& P) {
+  const int p = P.p, nc = P.nc;
+  std::vector<int> a(nc), b(nc), c(nc);
+  for (int i = 0; i < nc; i++) mi_decode(i, a[i], b[i], c[i]);
+  auto fact = [](int n) {
+    double f = 1;
+    for (int i = 2; i <= n; i++) f *= i;
+    return f;
+  };
+  auto neg_bits = [](int ja, int jb, int jc) {
+    int bits = 0;
+    for (int o = 0; o < 8; o++) {
+      int odd = ((o & 1) ? 0 : ja) + ((o & 2) ? 0 : jb) + ((o & 4) ? 0 : jc);
+      if (odd & 1) bits |= 1 << o;
+    }
+    return (uint8_t)bits;
+  };
+  std::vector<int32_t> moff(nc + 1), loff(nc + 1);
+  std::vector<TEnt> ment, lent;
+  for (int n = 0; n < nc; n++) {
+    moff[n] = (int32_t)ment.size();
+    for (int k = 0; k < nc; k++) {
+      if (a[k] > a[n] || b[k] > b[n] || c[k] > c[n]) continue;
+      const int ja = a[n] - a[k], jb = b[n] - b[k], jc = c[n] - c[k], tj = ja + jb + jc, tk = a[k] + b[k] + c[k];
+      const double cf = std::pow(0.25, tj) / (fact(ja) * fact(jb) * fact(jc)) * std::ldexp(1.0, -tk);
+      ment.push_back(TEnt{(uint16_t)k, neg_bits(ja, jb, jc), 0, (float)cf});
+    }
+  }
+  moff[nc] = (int32_t)ment.size();
+  for (int m = 0; m < nc; m++) {
+    loff[m] = (int32_t)lent.size();
+    const int tm = a[m] + b[m] + c[m];
+    for (int j = 0; j < nc; j++) {
+      const int tj = a[j] + b[j] + c[j];
+      if (tm + tj > p) continue;
+      const int k = mi_index(a[m] + a[j], b[m] + b[j], c[m] + c[j]);
+      const double cf = std::pow(0.5, tj) / (fact(a[j]) * fact(b[j]) * fact(c[j])) * std::ldexp(1.0, -(tm + tj));
+      lent.push_back(TEnt{(uint16_t)k, neg_bits(a[j], b[j], c[j]), 0, (float)cf});
+    }
+  }
+  loff[nc] = (int32_t)lent.size();
+  cudaStream_t s = P.stream;
+  P.m2m_eoff = dalloc<int32_t>(P, nc + 1);
+  P.m2m_ent = dalloc<TEnt>(P, ment.size());
+  P.l2l_eoff = dalloc<int32_t>(P, nc + 1);
+  P.l2l_ent = dalloc<TEnt>(P, lent.size());
+  DM_CUDA(cudaMemcpyAsync(P.m2m_eoff, moff.data(), moff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaMemcpyAsync(P.m2m_ent, ment.data(), ment.size() * sizeof(TEnt), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaMemcpyAsync(P.l2l_eoff, loff.data(), loff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaMemcpyAsync(P.l2l_ent, lent.data(), lent.size() * sizeof(TEnt), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
+// mass-lumped gradient (Sec. 4.1) as a sparse FP32 operator on u: row i holds,
+// for every node j sharing a tet with i, -(1/V_i) sum_{t ni i, j} vol_t grad lambda_j^t
+static void build_gradient_operator(Plan& P) {
+  cudaStream_t s = P.stream;
+  const int64_t nn = P.nn, nt = P.nt;
+  std::vector<int32_t> tets(4 * nt), nt_tet(4 * nt), perm(nn);
+  std::vector<double> grad(12 * nt), vol(nt);
+  std::vector<int64_t> nt_off(nn + 1);
+  DM_CUDA(cudaMemcpyAsync(tets.data(), P.tets_s, sizeof(int32_t) * 4 * nt, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(nt_tet.data(), P.nt_tet, sizeof(int32_t) * 4 * nt, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(perm.data(), P.node_perm, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(grad.data(), P.tet_grad, sizeof(double) * 12 * nt, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(vol.data(), P.tet_vol, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(nt_off.data(), P.nt_off, sizeof(int64_t) * (nn + 1), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> off(nn + 1, 0);
+  std::vector<int32_t> col;
+  std::vector<float4> w;
+  std::vector<std::pair<int32_t, std::array<double, 3>>> row;
+  for (int64_t i = 0; i < nn; i++) {
+    row.clear();
+    double V = 0;
+    for (int64_t e = nt_off[i]; e < nt_off[i + 1]; e++) {
+      const int64_t t = nt_tet[e];
+      V += vol[t];
+      for (int k = 0; k < 4; k++) {
+        const int32_t j = tets[4 * t + k];
+        auto it = std::find_if(row.begin(), row.end(), [&](const auto& x) { return x.first == j; });
+        if (it == row.end()) {
+          row.push_back({j, {0.0, 0.0, 0.0}});
+          it = row.end() - 1;
+        }
+        for (int d = 0; d < 3; d++) it->second[d] += vol[t] * grad[12 * t + 3 * k + d];
+      }
+    }
+    std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    if (V > 0)
+      for (auto& x : row) {
+        col.push_back(x.first);
+        w.push_back(make_float4((float)(-x.second[0] / V), (float)(-x.second[1] / V), (float)(-x.second[2] / V), 0.f));
+      }
+    off[i + 1] = (int64_t)col.size();
+  }
+  std::vector<int32_t> iperm(nn);
+  for (int64_t i = 0; i < nn; i++) iperm[perm[i]] = (int32_t)i;
+  P.hg_off = dalloc<int64_t>(P, nn + 1);
+  P.hg_col = dalloc<int32_t>(P, std::max<size_t>(col.size(), 1));
+  P.hg_w = dalloc<float4>(P, std::max<size_t>(w.size(), 1));
+  P.node_iperm = dalloc<int32_t>(P, nn);
+  DM_CUDA(cudaMemcpyAsync(P.hg_off, off.data(), sizeof(int64_t) * (nn + 1), cudaMemcpyHostToDevice, s));
+  if (!col.empty()) {
+    DM_CUDA(cudaMemcpyAsync(P.hg_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.hg_w, w.data(), sizeof(float4) * w.size(), cudaMemcpyHostToDevice, s));
+  }
+  DM_CUDA(cudaMemcpyAsync(P.node_iperm, iperm.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_mixed_operators(Plan& P) {
+  build_translations(P);
+  build_gradient_operator(P);
   cudaStream_t s = P.stream;
   P.Ghat32 = dalloc<float>(P, std::max<int64_t>(P.n_sup, 1) * P.nc1);
   if (!P.h_src_leaves.empty()) {
@@ -292,8 +469,9 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.begin(DEMAG_STAGE_P2M);
   DM_CUDA(cudaMemsetAsync(W.Q32, 0, sizeof(float) * P.ncells * nc * B, s));
   if (!P.h_src_leaves.empty()) {
-    k_p2m32<<<(unsigned)P.h_src_leaves.size(), 128, 0, s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32,
-                                                            nc, P.nc1, B, W.Q32);
+    dim3 grid((unsigned)P.h_src_leaves.size(), (unsigned)((nc + P2M_NN - 1) / P2M_NN),
+              (unsigned)((B + P2M_B - 1) / P2M_B));
+    k_p2m32<<<grid, P2M_B, 0, s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1, B, W.Q32);
     DM_LAUNCH("k_p2m32");
     clk.launched();
   }
@@ -301,7 +479,8 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.begin(DEMAG_STAGE_M2M);
   for (int l = P.nlevels - 2; l >= 0; l--) {
     int64_t lb = P.level_start[l], le = P.level_start[l + 1];
-    k_m2m32<<<(unsigned)(le - lb), 128, 0, s>>>(lb, P.cell_child0, P.cell_nchild, P.cell_prefix, p, nc, B, W.Q32);
+    k_m2m32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_child0, P.cell_nchild, P.cell_prefix,
+                                                          P.m2m_eoff, P.m2m_ent, nc, B, W.Q32);
     DM_LAUNCH("k_m2m32");
     clk.launched();
   }
@@ -325,14 +504,15 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.begin(DEMAG_STAGE_L2L);
   for (int l = 1; l < P.nlevels; l++) {
     int64_t lb = P.level_start[l], le = P.level_start[l + 1];
-    k_l2l32<<<(unsigned)(le - lb), 128, 0, s>>>(lb, P.cell_parent, P.cell_range, P.cell_prefix, p, nc, B, W.L32);
+    k_l2l32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_parent, P.cell_range, P.cell_prefix,
+                                                          P.l2l_eoff, P.l2l_ent, nc, B, W.L32);
     DM_LAUNCH("k_l2l32");
     clk.launched();
   }
   clk.end();
   clk.begin(DEMAG_STAGE_L2P);
-  k_l2p32<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, P.node_leaf, P.cell_level, P.nodes_s, P.cell_centre, P.side, p, nc, B,
-                                          W.L32, W.u32);
+  k_l2p32<<<nblk(P.nn * B, 256), 256, 0, s>>>(P.nn, P.node_leaf, P.cell_level, P.nodes_s, P.cell_centre, P.side, p,
+                                              nc, B, W.L32, W.u32);
   DM_LAUNCH("k_l2p32");
   clk.launched();
   clk.end();
@@ -349,12 +529,13 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
     clk.end();
   }
   clk.begin(DEMAG_STAGE_H);
-  if (!otf) {
-    k_u32_to_64<<<nblk(P.nn * B, 256), 256, 0, s>>>(P.nn * B, W.u32, W.u_s);
-    DM_LAUNCH("k_u32_to_64");
-    clk.launched();
+  if (otf) {
+    launch_lumped_H_out(P, B, W.u_s, ud, Hd, s);  // FP64 near field: u in FP64
+  } else {
+    k_out32<<<dim3((unsigned)((P.nn + 31) / 32), (unsigned)((B + 31) / 32)), 256, 0, s>>>(
+        P.nn, B, P.node_iperm, P.hg_off, P.hg_col, P.hg_w, W.u32, ud, Hd);
+    DM_LAUNCH("k_out32");
   }
-  launch_lumped_H_out(P, B, W.u_s, ud, Hd, s);
   clk.launched();
   clk.end();
   clk.finish();

@@ -309,6 +309,129 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_near_apply32_v2(
   }
 }
 
+// Batched form for B % 4 == 0: one block of NB_WARPS warps per (target leaf,
+// 128 states), so W is streamed from HBM once per evaluation.  Lane = 4
+// consecutive states (float4 loads of M), 16 target nodes per pass: 64
+// accumulators per lane, 12 FMAs per broadcast shared-memory read of W.  Each
+// warp stages its column chunks (NB_CW columns, <= 4 KB) into two buffers with
+// bulk copies, the next chunk in flight while the current one is used; the
+// warps' partial sums are added in shared memory at the end of the pass.
+constexpr int NB_WARPS = 8, NB_CW = 16, NB_NT = 16, NB_STATES = 128;
+
+__global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
+    const int32_t* __restrict__ targets, const int4* __restrict__ range, const int64_t* __restrict__ coloff,
+    const int32_t* __restrict__ cols, const int64_t* __restrict__ woff32, const float* __restrict__ W32,
+    const float* __restrict__ Ms, int B, float* u_s, int* err) {
+  extern __shared__ __align__(128) float4 sW[];  // NB_WARPS x 2 x (NB_CW * NB_NT) float4; then the reduction
+  __shared__ __align__(8) uint64_t bar[NB_WARPS][2];
+  __shared__ int s_bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
+  const float4* Wt = (const float4*)(W32 + woff32[ti]);
+  const int bs = blockIdx.y * NB_STATES + lane * 4;
+  const bool live = bs < B;
+  float4* const buf0 = sW + warp * 2 * NB_CW * NB_NT;  // buffer `slot` at buf0 + slot * NB_CW * NB_NT
+  if (lane == 0) {
+    mbar_init(&bar[warp][0]);
+    mbar_init(&bar[warp][1]);
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  uint32_t phases = 0u;  // bit s: parity of buffer s
+  const int nchunk = (int)((ncol + NB_CW - 1) / NB_CW);
+  for (int i0 = 0; i0 < nT; i0 += NB_NT) {
+    bool bad = false;
+    const int ni = min(NB_NT, nT - i0);
+    // lane 0 issues chunk k into buffer `slot`
+    auto issue = [&](int k, int slot) {
+      if (lane != 0) return;
+      const int64_t cb = (int64_t)k * NB_CW;
+      const int cc = (ncol - cb < NB_CW) ? (int)(ncol - cb) : NB_CW;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (ni == nT) {
+        tma_load(buf0 + slot * NB_CW * NB_NT, Wt + cb * nT, (uint32_t)(cc * nT * sizeof(float4)), &bar[warp][slot]);
+      } else {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[warp][slot])),
+                     "r"((uint32_t)(cc * ni * sizeof(float4)))
+                     : "memory");
+        for (int c = 0; c < cc; c++)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(buf0 + slot * NB_CW * NB_NT + c * ni)),
+              "l"(Wt + (cb + c) * nT + i0), "r"((uint32_t)(ni * sizeof(float4))), "r"(smem_u32(&bar[warp][slot]))
+              : "memory");
+      }
+    };
+    float acc[NB_NT][4];
+#pragma unroll
+    for (int i = 0; i < NB_NT; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    int q = 0;
+    if (warp < nchunk) issue(warp, 0);
+    for (int k = warp; k < nchunk && !bad; k += NB_WARPS, q++) {
+      const int slot = q & 1;
+      __syncwarp();  // every lane is done with the other buffer before it is refilled
+      if (k + NB_WARPS < nchunk) issue(k + NB_WARPS, slot ^ 1);
+      if (!mbar_wait(&bar[warp][slot], (phases >> slot) & 1u)) {
+        if (lane == 0) {
+          atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+          atomicExch(&s_bad, 1);
+        }
+        bad = true;
+        break;
+      }
+      phases ^= 1u << slot;
+      const int64_t cb = (int64_t)k * NB_CW;
+      const int cc = (ncol - cb < NB_CW) ? (int)(ncol - cb) : NB_CW;
+      const float4* w = buf0 + slot * NB_CW * NB_NT;
+      for (int c = 0; c < cc; c++) {
+        float4 mx = make_float4(0.f, 0.f, 0.f, 0.f), my = mx, mz = mx;
+        if (live) {
+          const float* mp = Ms + (int64_t)cols[c0 + cb + c] * 3 * B + bs;
+          mx = *(const float4*)mp;
+          my = *(const float4*)(mp + B);
+          mz = *(const float4*)(mp + 2 * B);
+        }
+        const float4* wc = w + c * ni;
+#pragma unroll
+        for (int i = 0; i < NB_NT; i++)
+          if (i < ni) {
+            const float4 wv = wc[i];
+            acc[i][0] = fmaf(wv.x, mx.x, fmaf(wv.y, my.x, fmaf(wv.z, mz.x, acc[i][0])));
+            acc[i][1] = fmaf(wv.x, mx.y, fmaf(wv.y, my.y, fmaf(wv.z, mz.y, acc[i][1])));
+            acc[i][2] = fmaf(wv.x, mx.z, fmaf(wv.y, my.z, fmaf(wv.z, mz.z, acc[i][2])));
+            acc[i][3] = fmaf(wv.x, mx.w, fmaf(wv.y, my.w, fmaf(wv.z, mz.w, acc[i][3])));
+          }
+      }
+    }
+    if (bad && lane == 0) {
+      // a wait expired: let this warp's copies in flight land (bounded) before the buffers are reused
+      mbar_wait(&bar[warp][0], phases & 1u);
+      mbar_wait(&bar[warp][1], (phases >> 1) & 1u);
+    }
+    // add the warps' partial sums: red[warp][i][128 states]
+    __syncthreads();
+    if (s_bad) return;  // uniform: read after the barrier
+    float4* red = sW;
+#pragma unroll
+    for (int i = 0; i < NB_NT; i++)
+      if (i < ni) red[(warp * NB_NT + i) * 32 + lane] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    __syncthreads();
+    const float* redf = (const float*)sW;
+    for (int idx = threadIdx.x; idx < ni * NB_STATES; idx += blockDim.x) {
+      const int i = idx / NB_STATES, sl = idx - i * NB_STATES;
+      float v = 0.f;
+#pragma unroll
+      for (int w2 = 0; w2 < NB_WARPS; w2++) v += redf[(w2 * NB_NT + i) * NB_STATES + sl];
+      const int b = blockIdx.y * NB_STATES + sl;
+      if (b < B) u_s[(int64_t)(rT.z + i0 + i) * B + b] += v;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 void build_near_field(Plan& P) {
@@ -402,6 +525,19 @@ void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStre
 void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s) {
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
   if (!nT) return;
+  if (B % 4 == 0) {
+    const size_t smem = sizeof(float4) * NB_WARPS * 2 * NB_CW * NB_NT;  // = the reduction area
+    static bool attr3 = false;
+    if (!attr3) {
+      DM_CUDA(cudaFuncSetAttribute(k_near_apply32_v3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr3 = true;
+    }
+    dim3 grid((unsigned)nT, (unsigned)((B + NB_STATES - 1) / NB_STATES));
+    k_near_apply32_v3<<<grid, NB_WARPS * 32, smem, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols,
+                                                        P.w_off32, P.W32, Ms, B, u_s, err);
+    DM_LAUNCH("k_near_apply32_v3");
+    return;
+  }
   const size_t smem = sizeof(float4) * NA_WARPS * NA_COLS * NA_NT;
   static bool attr = false;
   if (!attr) {
