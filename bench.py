@@ -164,21 +164,18 @@ def m2l_macs(p):
 
 
 def m2l_tile_flops(p, precision):
-    """Flops the tensor-core M2L issues per pair and state: sum over the level
-    groups of 2 * N_g * K_g (rows padded to 16, K padded to one 32-byte k-step),
-    times 3 for split BF16.  Same level-group choice as the kernel: a dynamic
-    programme minimising sum(N_g * K_g + 256) over contiguous degree ranges."""
+    """Flops the tensor-core M2L issues per pair and state: every k-step
+    (16 BF16 or 8 TF32 values of n) is one M = 128 MMA over the rows m still
+    needed at that k-step (rows of degree t need |n| < C(p - t + 3, 3)),
+    padded to 16; times 3 for split BF16."""
     cnc = lambda t: 0 if t < 0 else (t + 1) * (t + 2) * (t + 3) // 6
     pad = lambda x, m: (x + m - 1) // m * m
-    kstep = 16 if precision == "bf16x3" else 8
-    best = {0: (0, 0)}
-    for tb in range(1, p + 2):
-        cands = []
-        for ta in range(tb):
-            nk = pad(cnc(tb - 1) - cnc(ta - 1), 16) * pad(cnc(p - ta), kstep)
-            cands.append((best[ta][0] + nk + 256, best[ta][1] + nk))
-        best[tb] = min(cands)
-    return 2.0 * best[p + 1][1] * (3 if precision == "bf16x3" else 1)
+    kw = 16 if precision == "bf16x3" else 8
+    total = 0
+    for ks in range(pad(cnc(p), kw) // kw):
+        rows = max([cnc(t) for t in range(p + 1) if cnc(p - t) > ks * kw] or [0])
+        total += pad(rows, 16) * kw
+    return 2.0 * total * (3 if precision == "bf16x3" else 1)
 
 
 def alu_peak_tflops(kind, sm_mhz):
@@ -225,7 +222,7 @@ def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
                                     "measured bf16 burst (MEASURED_PEAKS.json)")
                                    + (" x 1.1/2.25 nominal TF32 ratio" if precision == "tf32" else ""),
                     "note": "achieved counts algorithmic flops 2*C(p+6,6) per pair per state; executed_tflops "
-                            "counts the padded level-blocked tiles issued to the tensor pipe "
+                            "counts the padded per-k-step row prefixes issued to the tensor pipe "
                             + ("(3 BF16 MMAs per tile)" if precision == "bf16x3" else "(1 TF32 MMA per tile)")})
         return out
     if work is not None:

@@ -63,29 +63,33 @@ __global__ void k_ghat32(const int32_t* __restrict__ leaves, const int32_t* __re
     }
 }
 
-// P2M: one block per (source leaf, 8 coefficients n, 128 states); the leaf's
-// Gt rows are staged in shared memory 16 support nodes at a time, with a zero
-// entry at index nc1 standing for "no such coefficient" (n_c = 0)
-constexpr int P2M_NN = 8, P2M_NE = 16, P2M_B = 128;
+// P2M: one block per (source leaf, 16 coefficients n, 128 states), thread =
+// state.  For 16 support nodes at a time the block gathers, per node, the 48
+// values Gt[n - e_c] its 16 coefficients need (0 where n_c = 0) into shared
+// memory in the order of use, so one node costs 12 broadcast 16-byte reads for
+// 48 FMAs; M of the next node is loaded while the current one is applied.
+constexpr int P2M_NN = 16, P2M_NE = 16, P2M_B = 128;
 
 __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ leaves,
                                                  const int64_t* __restrict__ sup_off,
                                                  const int32_t* __restrict__ sup_node, const float* __restrict__ G,
                                                  const float* __restrict__ Ms, int nc, int nc1, int B, float* Q) {
-  __shared__ float sG[P2M_NE][MAX_NCOEF + 1];
+  __shared__ __align__(16) float sG[P2M_NE][P2M_NN * 3];
+  __shared__ int six[P2M_NN * 3];
   const int32_t c = leaves[blockIdx.x];
   const int n0 = blockIdx.y * P2M_NN;
   const int b = blockIdx.z * P2M_B + threadIdx.x;
   const bool live = b < B;
-  int ix[P2M_NN][3];
-#pragma unroll
-  for (int j = 0; j < P2M_NN; j++) {
-    int na = 0, nb = 0, nz = 0;
-    const bool ok = n0 + j < nc;
-    if (ok) mi_decode(n0 + j, na, nb, nz);
-    ix[j][0] = (ok && na) ? mi_index(na - 1, nb, nz) : nc1;
-    ix[j][1] = (ok && nb) ? mi_index(na, nb - 1, nz) : nc1;
-    ix[j][2] = (ok && nz) ? mi_index(na, nb, nz - 1) : nc1;
+  if (threadIdx.x < P2M_NN * 3) {
+    const int j = threadIdx.x / 3, comp = threadIdx.x - 3 * j;
+    int na = 0, nb = 0, nz = 0, ix = -1;
+    if (n0 + j < nc) {
+      mi_decode(n0 + j, na, nb, nz);
+      if (comp == 0 && na) ix = mi_index(na - 1, nb, nz);
+      if (comp == 1 && nb) ix = mi_index(na, nb - 1, nz);
+      if (comp == 2 && nz) ix = mi_index(na, nb, nz - 1);
+    }
+    six[threadIdx.x] = ix;
   }
   float acc[P2M_NN];
 #pragma unroll
@@ -94,17 +98,37 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
   for (int64_t e0 = so; e0 < eo; e0 += P2M_NE) {
     const int ne = (int)min((int64_t)P2M_NE, eo - e0);
     __syncthreads();
-    for (int q = threadIdx.x; q < ne * (nc1 + 1); q += blockDim.x) {
-      const int r = q / (nc1 + 1), m = q - r * (nc1 + 1);
-      sG[r][m] = m < nc1 ? G[(e0 + r) * nc1 + m] : 0.f;
+    for (int q = threadIdx.x; q < ne * P2M_NN * 3; q += blockDim.x) {
+      const int r = q / (P2M_NN * 3), jc = q - r * (P2M_NN * 3);
+      const int ix = six[jc];
+      sG[r][jc] = ix >= 0 ? G[(e0 + r) * nc1 + ix] : 0.f;
     }
     __syncthreads();
     if (live) {
+      const float* mp = Ms + (int64_t)sup_node[e0] * 3 * B + b;
+      float m0 = mp[0], m1 = mp[B], m2 = mp[2 * B];
       for (int r = 0; r < ne; r++) {
-        const float* mp = Ms + (int64_t)sup_node[e0 + r] * 3 * B + b;
-        const float m0 = mp[0], m1 = mp[B], m2 = mp[2 * B];
+        float n0v = 0.f, n1v = 0.f, n2v = 0.f;
+        if (r + 1 < ne) {
+          const float* np = Ms + (int64_t)sup_node[e0 + r + 1] * 3 * B + b;
+          n0v = np[0];
+          n1v = np[B];
+          n2v = np[2 * B];
+        }
+        const float4* g4 = (const float4*)sG[r];
 #pragma unroll
-        for (int j = 0; j < P2M_NN; j++) acc[j] += sG[r][ix[j][0]] * m0 + sG[r][ix[j][1]] * m1 + sG[r][ix[j][2]] * m2;
+        for (int q = 0; q < P2M_NN * 3 / 4; q++) {
+          const float4 g = g4[q];  // values 4q .. 4q+3 = (j, comp) pairs in order
+          const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int jc = 4 * q + u, j = jc / 3, comp = jc % 3;
+            acc[j] = fmaf(gv[u], comp == 0 ? m0 : (comp == 1 ? m1 : m2), acc[j]);
+          }
+        }
+        m0 = n0v;
+        m1 = n1v;
+        m2 = n2v;
       }
     }
   }
@@ -212,26 +236,41 @@ __global__ void k_m2l32(const int32_t* __restrict__ targets, const int64_t* __re
   }
 }
 
-// L2L of one level: thread per (child cell, m, state), added to the child's
-// own M2L result
-__global__ void k_l2l32(int64_t lb, int64_t ncl, const int32_t* __restrict__ parent, const int4* __restrict__ range,
+// L2L from the parents of one level: thread per (parent, m, state) feeding all
+// children at once (each parent coefficient is loaded once; the octant only
+// flips signs); added to the children's own M2L results
+__global__ void k_l2l32(int64_t lb, int64_t ncl, const int32_t* __restrict__ child0,
+                        const int32_t* __restrict__ nchild, const int4* __restrict__ range,
                         const uint64_t* __restrict__ prefix, const int32_t* __restrict__ eoff,
                         const TEnt* __restrict__ ent, int nc, int B, float* L) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)nc * B;
   if (idx >= ncl * per) return;
-  const int64_t C = lb + idx / per;
-  const int4 r = range[C];
-  if (r.w == r.z) return;  // no target nodes below this cell
+  const int64_t P = lb + idx / per;
+  const int nch = nchild[P];
+  if (nch == 0) return;
   const int rem = (int)(idx % per), m = rem / B, b = rem - m * B;
-  const int oct = (int)(prefix[C] & 7ull);
-  const float* Lp = L + (int64_t)parent[C] * per + b;
-  float acc = 0.f;
+  const int32_t c0 = child0[P];
+  int oct[8];
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    oct[k] = k < nch ? (int)(prefix[c0 + k] & 7ull) : 0;
+    acc[k] = 0.f;
+  }
+  const float* Lp = L + P * per + b;
   for (int e = eoff[m], e1 = eoff[m + 1]; e < e1; e++) {
     const TEnt E = ent[e];
-    acc = fmaf(((E.neg >> oct) & 1) ? -E.c : E.c, Lp[(int64_t)E.k * B], acc);
+    const float v = E.c * Lp[(int64_t)E.k * B];
+#pragma unroll
+    for (int k = 0; k < 8; k++) acc[k] += ((E.neg >> oct[k]) & 1) ? -v : v;
   }
-  L[C * per + (int64_t)m * B + b] += acc;
+#pragma unroll
+  for (int k = 0; k < 8; k++)
+    if (k < nch) {
+      const int4 r = range[c0 + k];
+      if (r.w > r.z) L[(int64_t)(c0 + k) * per + (int64_t)m * B + b] += acc[k];  // only cells with target nodes
+    }
 }
 
 // L2P: thread per (node, state); u = sum_m Lt_m s_m(z/s) over the node's leaf
@@ -502,10 +541,10 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   }
   clk.end();
   clk.begin(DEMAG_STAGE_L2L);
-  for (int l = 1; l < P.nlevels; l++) {
+  for (int l = 0; l + 1 < P.nlevels; l++) {  // parents at level l, children at l + 1
     int64_t lb = P.level_start[l], le = P.level_start[l + 1];
-    k_l2l32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_parent, P.cell_range, P.cell_prefix,
-                                                          P.l2l_eoff, P.l2l_ent, nc, B, W.L32);
+    k_l2l32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_child0, P.cell_nchild, P.cell_range,
+                                                          P.cell_prefix, P.l2l_eoff, P.l2l_ent, nc, B, W.L32);
     DM_LAUNCH("k_l2l32");
     clk.launched();
   }

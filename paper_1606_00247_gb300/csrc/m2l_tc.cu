@@ -12,13 +12,14 @@
 // v_S = (c_T - c_S) / s_T is fixed by the level difference and an integer
 // lattice offset: 2 v = (2 k_T + 1) - (2 k_S + 1) 2^dl for dl = l_T - l_S >= 0,
 // and 2^(1-dl) v = (2 k_T + 1) 2^-dl - (2 k_S + 1) otherwise (k = integer box
-// coordinates).  A ball of 224k tets has ~5k distinct (dl, offset) keys for
+// coordinates).  A ball of 224k tets has ~8k distinct (dl, offset) keys for
 // ~870k pairs, so every distinct K is built once per plan (FP64 b_k, rounded
 // to the operand format) into a table, and each pair carries the index of its
-// operator.  K is triangular in the degrees of (m, n): rows are cut into
-// level groups [ta, tb) chosen by a small dynamic programme, group g
-// multiplying only the n with |n| <= p - ta (dense tiles cover ~2.6x the
-// useful entries at p = 8 instead of ~9x).
+// operator.  K is triangular in the degrees of (m, n): a row of degree t needs
+// only the n with |n| <= p - t, so at k-step ks (n in [ks KW, (ks+1) KW)) the
+// rows still needed are a prefix of the graded order; each k-step is one MMA
+// over that prefix (N = its length padded to 16; the padding rows hold exact
+// zeros of the operator), accumulating into TMEM column m for row m.
 //
 // Operand formats:
 //   TF32   : one MMA per k-step (kind::tf32) -- ~2e-4 relative error on u;
@@ -66,7 +67,6 @@ namespace {
 
 constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;              // states per CTA = MMA M = TMEM lanes
-constexpr int TC_MAXG = 8;
 constexpr int TC_MAXKS = 48;
 constexpr int TC_SLICE = TC_M * 32;    // one k-step of one operand copy: 128 rows x 32 bytes
 constexpr int TC_MAXNC = 512;          // b_k table of the operator build (p <= 12)
@@ -91,78 +91,41 @@ struct Tmp {
 struct TcLayout {
   int valid, bf16, ncopy;
   int E, KW;                        // elements per 16 bytes, per k-step (2E)
-  int ng;                           // level groups, K non-increasing in g
-  int m0[TC_MAXG], nrow[TC_MAXG];   // rows [m0, m0 + nrow) of the graded order
-  int N[TC_MAXG], K[TC_MAXG];       // rows padded to 16 (MMA N), n count padded to a k-step
-  int col[TC_MAXG];                 // first TMEM column of the group
-  int rowpre[TC_MAXG + 1];          // sum of N over the groups before g
-  int KS;                           // k-steps of the A tile (K[0] / KW)
-  int na[TC_MAXKS];                 // groups active at k-step ks (a prefix)
+  int nc, ncp;                      // coefficients, padded to 16 (TMEM columns used)
+  int KS;                           // k-steps of the A tile
+  int Nks[TC_MAXKS];                // rows used at k-step ks (a prefix), padded to 16
   int ks_off[TC_MAXKS + 1];         // byte offset of k-step ks within one operator
   int op_bytes;                     // one operator, all k-steps, all copies
   int a_bytes;                      // A slice of one k-step, all copies
-  int tmem_cols;                    // power of two >= sum of N
+  int tmem_cols;                    // power of two >= ncp
 };
 
 __host__ __device__ constexpr int cnc_of(int t) { return t < 0 ? 0 : (t + 1) * (t + 2) * (t + 3) / 6; }
 __host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
 
-// level groups minimise sum over groups of (N_g K_g + 256); then the layout
 __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16) {
   TcLayout G{};
-  if (p < 1 || p > 12 || cnc_of(p) > TC_MAXNC) return G;
+  if (p < 1 || p > 12) return G;
   G.bf16 = bf16 ? 1 : 0;
   G.ncopy = bf16 ? 2 : 1;
   G.E = bf16 ? 8 : 4;
   G.KW = 2 * G.E;
-  const int T = p + 1;
-  long best[16] = {};
-  int from[16] = {};
-  for (int i = 0; i <= T; i++) best[i] = -1;
-  best[0] = 0;
-  for (int tb = 1; tb <= T; tb++)  // groups cover degrees [ta, tb)
-    for (int ta = 0; ta < tb; ta++) {
-      if (best[ta] < 0) continue;
-      const long cost = (long)pad_to(cnc_of(tb - 1) - cnc_of(ta - 1), 16) * pad_to(cnc_of(p - ta), G.KW) + 256;
-      if (best[tb] < 0 || best[ta] + cost < best[tb]) {
-        best[tb] = best[ta] + cost;
-        from[tb] = ta;
-      }
-    }
-  int ta_of[16] = {}, tb_of[16] = {}, ng = 0;
-  for (int tb = T; tb > 0; tb = from[tb]) {
-    ta_of[ng] = from[tb];
-    tb_of[ng] = tb;
-    ng++;
-  }
-  if (ng > TC_MAXG) return G;
-  G.ng = ng;
-  int col = 0;
-  for (int g = 0; g < ng; g++) {  // ascending degrees
-    const int ta = ta_of[ng - 1 - g], tb = tb_of[ng - 1 - g];
-    G.m0[g] = cnc_of(ta - 1);
-    G.nrow[g] = cnc_of(tb - 1) - cnc_of(ta - 1);
-    G.N[g] = pad_to(G.nrow[g], 16);
-    if (G.N[g] > 256) return TcLayout{};  // MMA N limit for M = 128
-    G.K[g] = pad_to(cnc_of(p - ta), G.KW);
-    G.col[g] = col;
-    G.rowpre[g] = col;
-    col += G.N[g];
-  }
-  G.rowpre[ng] = col;
-  G.KS = G.K[0] / G.KW;
+  G.nc = cnc_of(p);
+  G.ncp = pad_to(G.nc, 16);
+  G.KS = pad_to(G.nc, G.KW) / G.KW;
   if (G.KS > TC_MAXKS) return TcLayout{};
   G.ks_off[0] = 0;
   for (int ks = 0; ks < G.KS; ks++) {
-    int na = 0;
-    while (na < ng && G.K[na] > ks * G.KW) na++;
-    G.na[ks] = na;
-    G.ks_off[ks + 1] = G.ks_off[ks] + G.ncopy * 32 * G.rowpre[na];
+    int rows = 0;  // rows of degree t need n < cnc(p - t)
+    for (int t = 0; t <= p; t++)
+      if (cnc_of(p - t) > ks * G.KW) rows = cnc_of(t);
+    G.Nks[ks] = pad_to(rows, 16);
+    G.ks_off[ks + 1] = G.ks_off[ks] + G.ncopy * 32 * G.Nks[ks];
   }
   G.op_bytes = G.ks_off[G.KS];
   G.a_bytes = G.ncopy * TC_SLICE;
   int tc = 32;
-  while (tc < col) tc *= 2;
+  while (tc < G.ncp) tc *= 2;
   if (tc > 512) return TcLayout{};
   G.tmem_cols = tc;
   G.valid = 1;
@@ -376,25 +339,23 @@ __global__ void __launch_bounds__(128) k_m2l_tc_ops(const int4* __restrict__ key
   unsigned char* out = ops + (int64_t)blockIdx.x * G.op_bytes;
   for (int ks = 0; ks < G.KS; ks++) {
     unsigned char* chunk = out + G.ks_off[ks];
-    for (int g = 0; g < G.na[ks]; g++) {
-      unsigned char* tile = chunk + G.ncopy * 32 * G.rowpre[g];
-      for (int it = tid; it < 2 * G.N[g]; it += blockDim.x) {
-        const int r = it >> 1, kc = it & 1;
-        double v[E];
-        for (int u = 0; u < E; u++) {
-          v[u] = 0.0;
-          const int n = ks * G.KW + kc * E + u;
-          if (r < G.nrow[g] && n < nc) {
-            int ma, mb, mz, na, nb, nz;
-            mi_decode(G.m0[g] + r, ma, mb, mz);
-            mi_decode(n, na, nb, nz);
-            const int tn = na + nb + nz;
-            if (tn + ma + mb + mz <= p) v[u] = b[idx3(na + ma, nb + mb, nz + mz)] * ldexp(1.0, dl * tn);
-          }
+    const int N = G.Nks[ks];
+    for (int it = tid; it < 2 * N; it += blockDim.x) {
+      const int r = it >> 1, kc = it & 1;  // row m = r, 16-byte column group kc of the k-step
+      double v[E];
+      for (int u = 0; u < E; u++) {
+        v[u] = 0.0;
+        const int n = ks * G.KW + kc * E + u;
+        if (r < nc && n < nc) {
+          int ma, mb, mz, na, nb, nz;
+          mi_decode(r, ma, mb, mz);
+          mi_decode(n, na, nb, nz);
+          const int tn = na + nb + nz;
+          if (tn + ma + mb + mz <= p) v[u] = b[idx3(na + ma, nb + mb, nz + mz)] * ldexp(1.0, dl * tn);
         }
-        const int off = (r >> 3) * 256 + kc * 128 + (r & 7) * 16;
-        store_row64<BF16>(tile + off, tile + 32 * G.N[g] + off, v);
       }
+      const int off = (r >> 3) * 256 + kc * 128 + (r & 7) * 16;
+      store_row64<BF16>(chunk + off, chunk + 32 * N + off, v);
     }
   }
 }
@@ -510,16 +471,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           if (!bad) {
             const uint32_t as = sa + j * G.a_bytes;
             const uint64_t ad = sdesc(as);
+            const uint32_t kc = kb0 + G.ks_off[ks];  // k-step chunk: hi rows, then lo rows
 #pragma unroll
-            for (int g = 0; g < TC_MAXG; g++) {
-              if (g < G.na[ks]) {
-                const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, G.N[g]);
-                const uint32_t kg = kb0 + G.ks_off[ks] + G.ncopy * 32 * G.rowpre[g];
-                const uint64_t bd = sdesc(kg);
-                mma<BF16>(tmem + G.col[g], ad, bd, id, ks == 0 ? acc : 1u);
+            for (int r0 = 0; r0 < 512; r0 += 256) {
+              if (r0 < G.Nks[ks]) {
+                const int nrow = (G.Nks[ks] - r0 < 256) ? G.Nks[ks] - r0 : 256;  // MMA N <= 256
+                const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, nrow);
+                const uint64_t bd = sdesc(kc + 32 * r0);
+                mma<BF16>(tmem + r0, ad, bd, id, ks == 0 ? acc : 1u);
                 if constexpr (BF16) {
-                  mma<BF16>(tmem + G.col[g], ad, sdesc(kg + 32 * G.N[g]), id, 1u);  // hi x lo
-                  mma<BF16>(tmem + G.col[g], sdesc(as + TC_SLICE), bd, id, 1u);     // lo x hi
+                  mma<BF16>(tmem + r0, ad, sdesc(kc + 32 * G.Nks[ks] + 32 * r0), id, 1u);  // hi x lo
+                  mma<BF16>(tmem + r0, sdesc(as + TC_SLICE), bd, id, 1u);                  // lo x hi
                 }
               }
             }
@@ -555,17 +517,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       const int b = sb * TC_M + q * 32 + lane;
       float* Lt = L + (int64_t)T * nc * B + b;
 #pragma unroll
-      for (int g = 0; g < G.ng; g++) {
+      for (int c0 = 0; c0 < G.ncp; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        if (b < B) {
 #pragma unroll
-        for (int c0 = 0; c0 < G.N[g]; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(G.col[g] + c0), r);
-          if (b < B) {
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-              const int m = G.m0[g] + c0 + i;
-              if (c0 + i < G.nrow[g]) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
-            }
+          for (int i = 0; i < 16; i++) {
+            const int m = c0 + i;
+            if (m < G.nc) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
           }
         }
       }

@@ -369,11 +369,18 @@ __global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
 #pragma unroll
     for (int i = 0; i < NB_NT; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
     int q = 0;
+    // column ids of the warp's current and next chunk: lane l holds column l of the chunk
+    auto chunk_cols = [&](int k) {
+      const int64_t cb = (int64_t)k * NB_CW;
+      return (k < nchunk && lane < NB_CW && cb + lane < ncol) ? cols[c0 + cb + lane] : 0;
+    };
+    int colv = chunk_cols(warp);
     if (warp < nchunk) issue(warp, 0);
     for (int k = warp; k < nchunk && !bad; k += NB_WARPS, q++) {
       const int slot = q & 1;
       __syncwarp();  // every lane is done with the other buffer before it is refilled
       if (k + NB_WARPS < nchunk) issue(k + NB_WARPS, slot ^ 1);
+      const int colv_next = chunk_cols(k + NB_WARPS);
       if (!mbar_wait(&bar[warp][slot], (phases >> slot) & 1u)) {
         if (lane == 0) {
           atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
@@ -386,13 +393,25 @@ __global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
       const int64_t cb = (int64_t)k * NB_CW;
       const int cc = (ncol - cb < NB_CW) ? (int)(ncol - cb) : NB_CW;
       const float4* w = buf0 + slot * NB_CW * NB_NT;
-      for (int c = 0; c < cc; c++) {
-        float4 mx = make_float4(0.f, 0.f, 0.f, 0.f), my = mx, mz = mx;
+      // M of column c is loaded while column c - 1 is applied
+      float4 mx = make_float4(0.f, 0.f, 0.f, 0.f), my = mx, mz = mx;
+      {
+        const int col = __shfl_sync(0xffffffffu, colv, 0);
         if (live) {
-          const float* mp = Ms + (int64_t)cols[c0 + cb + c] * 3 * B + bs;
+          const float* mp = Ms + (int64_t)col * 3 * B + bs;
           mx = *(const float4*)mp;
           my = *(const float4*)(mp + B);
           mz = *(const float4*)(mp + 2 * B);
+        }
+      }
+      for (int c = 0; c < cc; c++) {
+        float4 nx = make_float4(0.f, 0.f, 0.f, 0.f), ny = nx, nz = nx;
+        const int coln = __shfl_sync(0xffffffffu, colv, (c + 1) & 31);
+        if (live && c + 1 < cc) {
+          const float* mp = Ms + (int64_t)coln * 3 * B + bs;
+          nx = *(const float4*)mp;
+          ny = *(const float4*)(mp + B);
+          nz = *(const float4*)(mp + 2 * B);
         }
         const float4* wc = w + c * ni;
 #pragma unroll
@@ -404,7 +423,11 @@ __global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
             acc[i][2] = fmaf(wv.x, mx.z, fmaf(wv.y, my.z, fmaf(wv.z, mz.z, acc[i][2])));
             acc[i][3] = fmaf(wv.x, mx.w, fmaf(wv.y, my.w, fmaf(wv.z, mz.w, acc[i][3])));
           }
+        mx = nx;
+        my = ny;
+        mz = nz;
       }
+      colv = colv_next;
     }
     if (bad && lane == 0) {
       // a wait expired: let this warp's copies in flight land (bounded) before the buffers are reused
