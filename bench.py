@@ -386,7 +386,8 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}", "n_cells": st0["n_cells"], "n_m2l": st0["n_m2l"],
                    "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
                    "plan_ms": st0["plan_ms"], "m2l_operators": st0["n_m2l_ops"],
-                   "m2l_ring": {"kps": st0["m2l_kps"], "bytes": st0["m2l_ring_bytes"],
+                   "m2l_ring": {"targets_per_cta": st0["m2l_targets_per_cta"], "kps": st0["m2l_kps"],
+                                "bytes": st0["m2l_ring_bytes"],
                                 "autotuned": bool(args.autotune)}},
         "roofline": roof,
         "fp64_reference": ref_info,

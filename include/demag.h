@@ -75,10 +75,17 @@ typedef struct {
   int profile;         /* 1: time every stage of demag_eval with CUDA events
                           on the eval stream (adds one synchronisation per
                           call); read with demag_plan_stats                  */
+  int m2l_targets_per_cta; /* tensor-core M2L launch shape (TF32 / split BF16,
+                          p in {4, 6, 8, 10}): target cells sharing each
+                          source's moments in one CTA, 1 or 2; 0 = default
+                          (1) or the autotuner's choice                     */
+  int m2l_kps;         /* tensor-core M2L: k-steps per shared-memory slot,
+                          1..8; 0 = default (2) or the autotuner's choice.
+                          Every launch shape gives bit-identical results.   */
 } demag_options;
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
- * autotune=0, profile=0. */
+ * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and
@@ -176,6 +183,8 @@ typedef struct {
                             the tensor-core M2L (0: CUDA-core M2L)          */
   int m2l_kps;           /* tensor-core M2L ring: k-steps per slot          */
   int m2l_ring_bytes;    /* tensor-core M2L ring: shared memory per CTA     */
+  int m2l_targets_per_cta; /* tensor-core M2L: target cells sharing each
+                            source's moments in one CTA (1 or 2)            */
 } demag_stats;
 
 demag_status demag_plan_stats(demag_plan plan, demag_stats* out);

@@ -26,7 +26,8 @@ DEMAG_MIXED_BF16X3 = 3
 
 class demag_options(C.Structure):
     _fields_ = [("p", C.c_int), ("leaf_size", C.c_int), ("theta", C.c_double), ("precision", C.c_int),
-                ("near_mode", C.c_int), ("max_batch", C.c_int), ("autotune", C.c_int), ("profile", C.c_int)]
+                ("near_mode", C.c_int), ("max_batch", C.c_int), ("autotune", C.c_int), ("profile", C.c_int),
+                ("m2l_targets_per_cta", C.c_int), ("m2l_kps", C.c_int)]
 
 
 DEMAG_N_STAGES = 9
@@ -41,7 +42,8 @@ class demag_stats(C.Structure):
                 ("leaf_size", C.c_int), ("precision", C.c_int), ("near_mode", C.c_int), ("max_batch", C.c_int),
                 ("theta", C.c_double), ("eval_launches", C.c_int64), ("n_evals_profiled", C.c_int64),
                 ("stage_ms", C.c_double * DEMAG_N_STAGES), ("stage_launches", C.c_int64 * DEMAG_N_STAGES),
-                ("n_m2l_ops", C.c_int64), ("m2l_kps", C.c_int), ("m2l_ring_bytes", C.c_int)]
+                ("n_m2l_ops", C.c_int64), ("m2l_kps", C.c_int), ("m2l_ring_bytes", C.c_int),
+                ("m2l_targets_per_cta", C.c_int)]
 
 
 class demag_tree_export(C.Structure):

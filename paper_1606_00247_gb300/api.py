@@ -29,7 +29,7 @@ class Plan:
     """Tree, lists and operators of one mesh (demag_plan_create)."""
 
     def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
-                 device="cuda", profile=False, autotune=False):
+                 device="cuda", profile=False, autotune=False, m2l_targets_per_cta=0, m2l_kps=0):
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
@@ -40,6 +40,8 @@ class Plan:
         opt.max_batch = int(max_batch)
         opt.profile = int(bool(profile))
         opt.autotune = int(bool(autotune))
+        opt.m2l_targets_per_cta = int(m2l_targets_per_cta)
+        opt.m2l_kps = int(m2l_kps)
         with torch.cuda.device(self.device):
             st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
                                         int(leaf_size), float(theta), opt)

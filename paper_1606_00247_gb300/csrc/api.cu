@@ -102,6 +102,8 @@ void demag_options_default(demag_options* o) {
   o->near_mode = 0;
   o->max_batch = 1;
   o->autotune = 0;
+  o->m2l_targets_per_cta = 0;
+  o->m2l_kps = 0;
   o->profile = 0;
 }
 
@@ -125,6 +127,9 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
     if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
     if (o.autotune != 0 && o.autotune != 1) fail(DEMAG_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o.m2l_targets_per_cta < 0 || o.m2l_targets_per_cta > 2)
+      fail(DEMAG_ERR_INVALID_ARG, "m2l_targets_per_cta must be 0, 1 or 2");
+    if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X3)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
@@ -204,6 +209,7 @@ demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
   o->n_m2l_ops = plan->n_tc_ops;
   o->m2l_kps = plan->tc_kps;
   o->m2l_ring_bytes = plan->tc_budget;
+  o->m2l_targets_per_cta = plan->tc_ops ? plan->tc_nt : 0;
   return DEMAG_OK;
 }
 

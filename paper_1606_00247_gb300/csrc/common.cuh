@@ -169,7 +169,13 @@ struct Plan {
   int64_t n_tc_ops = 0;
   unsigned char* tc_ops = nullptr;
   int32_t* m2l_op = nullptr;        // n_m2l
-  int tc_kps = 0, tc_budget = 0;    // ring shape of the M2L kernel: k-steps per slot, ring bytes
+  int tc_nt = 1, tc_kps = 0, tc_budget = 0;  // M2L launch shape: targets per CTA, k-steps per slot, ring bytes
+  int64_t* tc_g1_off = nullptr;     // one-target groups: list offsets in target order
+  int64_t tc_n_g2 = 0;              // two-target groups (consecutive targets), union lists:
+  int32_t* tc_g2_tgt = nullptr;     //   2 per group, -1 = none
+  int64_t* tc_g2_off = nullptr;
+  int32_t* tc_g2_src = nullptr;
+  int32_t* tc_g2_op = nullptr;      //   2 per entry: each target's operator, -1 = not in its list
 
   // FP32 octree translations as coefficient lists (mixed precision):
   //   M2M: Qt^P_n += sum over entries e of n: sign_e(octant) c_e Qt^C_{k_e}

@@ -135,15 +135,18 @@ __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16) {
 // the orders with a compiled tensor-core kernel
 constexpr bool tc_order(int p) { return p == 4 || p == 6 || p == 8 || p == 10; }
 
-// ring shape of one launch: `kps` k-steps of one source per slot
+// launch shape: `nt` targets per CTA sharing each source's moments, `kps`
+// k-steps of one source per ring slot (A slices, then one K region per target)
 struct TcRing {
-  int kps, nsteps, slot_bytes, nslots;
+  int nt, kps, nsteps, kmax, slot_bytes, nslots;
   int step_koff[TC_MAXKS], step_kb[TC_MAXKS];  // K bytes of step st within one operator
 };
 
-bool make_ring(const TcLayout& G, int kps, int budget, TcRing& R) {
-  if (!G.valid || kps < 1 || kps > G.KS) return false;
+bool make_ring(const TcLayout& G, int nt, int kps, int budget, TcRing& R) {
+  if (!G.valid || kps < 1 || kps > G.KS || nt < 1 || nt > 2) return false;
+  if (nt == 2 && G.tmem_cols > 256) return false;  // two accumulators in one CTA's 512 columns
   R = TcRing{};
+  R.nt = nt;
   R.kps = kps;
   R.nsteps = (G.KS + kps - 1) / kps;
   int maxk = 0;
@@ -153,7 +156,8 @@ bool make_ring(const TcLayout& G, int kps, int budget, TcRing& R) {
     R.step_kb[st] = G.ks_off[k1] - G.ks_off[k0];
     maxk = std::max(maxk, R.step_kb[st]);
   }
-  R.slot_bytes = pad_to(kps * G.a_bytes + maxk, 1024);
+  R.kmax = maxk;
+  R.slot_bytes = pad_to(kps * G.a_bytes + nt * maxk, 1024);
   R.nslots = std::min(32, budget / R.slot_bytes);
   return R.nslots >= 2;
 }
@@ -181,8 +185,8 @@ __host__ __device__ constexpr uint32_t idesc(int fmt, int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
   uint32_t ok;
@@ -368,38 +372,46 @@ __host__ __device__ constexpr int degree_of(int m) {
 }
 
 // ---------------------------------------------------------------------------
-template <int P, bool BF16>
-__global__ void __launch_bounds__(TC_THREADS, 2)
-    k_m2l_tc(const int32_t* __restrict__ targets, const int64_t* __restrict__ m2l_off,
-             const int32_t* __restrict__ m2l_src, const int32_t* __restrict__ m2l_op,
-             const int32_t* __restrict__ level, double side, int nc, int B, int nsb, const TcRing R,
-             const unsigned char* __restrict__ QP, const unsigned char* __restrict__ ops, float* L, int* err) {
+// one CTA per group of NT targets (NT = 2: two consecutive targets, most often
+// siblings) and 128 states.  The group's sources are the union of the
+// targets' lists; gop[e * NT + t] is target t's operator for source e, or -1
+// when e is not in its list.  Warp 0 lane 0 streams each source's A slices
+// once, plus the K slices of every target that uses it; warp 1 (target 0) and
+// warp 3 (target 1) issue the MMAs into their own 256-column halves of TMEM.
+template <int P, bool BF16, int NT>
+__global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
+    k_m2l_tc(const int32_t* __restrict__ gtarget, const int64_t* __restrict__ goff,
+             const int32_t* __restrict__ gsrc, const int32_t* __restrict__ gop, const int32_t* __restrict__ level,
+             double side, int nc, int B, int nsb, const TcRing R, const unsigned char* __restrict__ QP,
+             const unsigned char* __restrict__ ops, float* L, int* err) {
   constexpr TcLayout G = tc_layout(P, BF16);
   static_assert(G.valid, "no tensor-core layout for this order");
+  static_assert(NT == 1 || G.tmem_cols <= 256, "two targets need two 256-column accumulators");
+  constexpr int TMEM_COLS = NT == 1 ? G.tmem_cols : 512;
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* full = (uint64_t*)(sm + (size_t)R.nslots * R.slot_bytes);
   uint64_t* empty = full + R.nslots;
   uint64_t* done = empty + R.nslots;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int* counts = (int*)(tmem_slot + 2);  // slots issued, slots consumed
+  int* counts = (int*)(tmem_slot + 2);  // slots issued, slots consumed by each issuer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int32_t T = targets[blockIdx.x];
+  const int64_t grp = blockIdx.x;
   const int sb = blockIdx.y;
-  const int64_t e0 = m2l_off[T], e1 = m2l_off[T + 1];
+  const int64_t e0 = goff[grp], e1 = goff[grp + 1];
   if (tid == 0) {
     for (int i = 0; i < R.nslots; i++) {
-      mbar_init(&full[i]);
-      mbar_init(&empty[i]);
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NT);  // one commit per issuer
     }
-    mbar_init(done);
+    mbar_init(done, NT);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
-    counts[0] = counts[1] = 0;
+    counts[0] = counts[1] = counts[2] = 0;
   }
-  if (warp == 2) {  // tensor memory for the accumulators of all groups
+  if (warp == 2) {  // tensor memory for the accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(G.tmem_cols)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -410,19 +422,23 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   const uint32_t ring0 = smem_u32(sm), full0 = smem_u32(full), empty0 = smem_u32(empty);
 
   if (warp == 0) {
-    // ---- producer: the A and K slices of every (source, step) into the ring
+    // ---- producer: A slices of every (source, step) once, K slices per target using it
     if (lane == 0) {
       int slot = 0, n = 0;
       uint32_t phase = 0;
-      int32_t S = m2l_src[e0], O = m2l_op[e0];
+      int32_t S = gsrc[e0], O[NT];
+#pragma unroll
+      for (int t = 0; t < NT; t++) O[t] = gop[e0 * NT + t];
       for (int64_t e = e0; e < e1 && !*abort_flag; e++) {
-        int32_t Sn = 0, On = 0;
-        if (e + 1 < e1) {  // next pair's indices, ahead of their use
-          Sn = m2l_src[e + 1];
-          On = m2l_op[e + 1];
+        int32_t Sn = 0, On[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) On[t] = -1;
+        if (e + 1 < e1) {  // next source's indices, ahead of their use
+          Sn = gsrc[e + 1];
+#pragma unroll
+          for (int t = 0; t < NT; t++) On[t] = gop[(e + 1) * NT + t];
         }
         const unsigned char* a = QP + ((int64_t)S * nsb + sb) * (int64_t)(G.KS * G.a_bytes);
-        const unsigned char* k = ops + (int64_t)O * G.op_bytes;
         for (int st = 0; st < R.nsteps; st++) {
           if (n >= R.nslots && !mbar_wait(empty0 + 8 * slot, phase ^ 1u, abort_flag)) {
             if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
@@ -432,9 +448,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           const int k0 = st * R.kps;
           const uint32_t fb = full0 + 8 * slot, dst = ring0 + slot * R.slot_bytes;
           const uint32_t ab = (uint32_t)(min(R.kps, G.KS - k0) * G.a_bytes), kb = (uint32_t)R.step_kb[st];
-          expect_tx(fb, ab + kb);
+          uint32_t bytes = ab;
+#pragma unroll
+          for (int t = 0; t < NT; t++) bytes += O[t] >= 0 ? kb : 0u;
+          expect_tx(fb, bytes);
           bulk_load(dst, a + (int64_t)k0 * G.a_bytes, ab, fb);
-          bulk_load(dst + R.kps * G.a_bytes, k + R.step_koff[st], kb, fb);
+#pragma unroll
+          for (int t = 0; t < NT; t++)
+            if (O[t] >= 0)
+              bulk_load(dst + R.kps * G.a_bytes + t * R.kmax, ops + (int64_t)O[t] * G.op_bytes + R.step_koff[st], kb,
+                        fb);
           n++;
           if (++slot == R.nslots) {
             slot = 0;
@@ -442,18 +465,23 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           }
         }
         S = Sn;
-        O = On;
+#pragma unroll
+        for (int t = 0; t < NT; t++) O[t] = On[t];
       }
       counts[0] = n;
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // ---- MMA issue: one thread; the MMAs of a source are unrolled
+  } else if (warp == 1 || (NT == 2 && warp == 3)) {
+    // ---- MMA issue for target t: one thread; the MMAs of a source are unrolled
+    const int t = warp == 1 ? 0 : 1;
     if (lane == 0) {
       int slot = 0, n = 0;
-      uint32_t phase = 0, acc = 0;  // acc = 0: the first k-step of the first source overwrites D
+      uint32_t phase = 0, acc = 0;  // acc = 0 until the first source of this target has started D
       bool bad = false;
+      // one target per CTA: every source is in its list, no operator index is needed here
+      int32_t O = NT == 1 ? 0 : gop[e0 * NT + t];
       for (int64_t e = e0; e < e1 && !bad; e++) {
+        const int32_t On = NT == 1 ? 0 : (e + 1 < e1 ? gop[(e + 1) * NT + t] : -1);
         int j = 0;
         uint32_t sa = 0, kb0 = 0;
 #pragma unroll
@@ -466,27 +494,30 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             }
             tc_fence_after();
             sa = ring0 + slot * R.slot_bytes;
-            kb0 = sa + R.kps * G.a_bytes - G.ks_off[ks];
+            kb0 = sa + R.kps * G.a_bytes + t * R.kmax - G.ks_off[ks];
           }
           if (!bad) {
-            const uint32_t as = sa + j * G.a_bytes;
-            const uint64_t ad = sdesc(as);
-            const uint32_t kc = kb0 + G.ks_off[ks];  // k-step chunk: hi rows, then lo rows
+            if (O >= 0) {
+              const uint32_t as = sa + j * G.a_bytes;
+              const uint64_t ad = sdesc(as);
+              const uint32_t kc = kb0 + G.ks_off[ks];  // k-step chunk: hi rows, then lo rows
 #pragma unroll
-            for (int r0 = 0; r0 < 512; r0 += 256) {
-              if (r0 < G.Nks[ks]) {
-                const int nrow = (G.Nks[ks] - r0 < 256) ? G.Nks[ks] - r0 : 256;  // MMA N <= 256
-                const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, nrow);
-                const uint64_t bd = sdesc(kc + 32 * r0);
-                mma<BF16>(tmem + r0, ad, bd, id, ks == 0 ? acc : 1u);
-                if constexpr (BF16) {
-                  mma<BF16>(tmem + r0, ad, sdesc(kc + 32 * G.Nks[ks] + 32 * r0), id, 1u);  // hi x lo
-                  mma<BF16>(tmem + r0, sdesc(as + TC_SLICE), bd, id, 1u);                  // lo x hi
+              for (int r0 = 0; r0 < 512; r0 += 256) {
+                if (r0 < G.Nks[ks]) {
+                  const int nrow = (G.Nks[ks] - r0 < 256) ? G.Nks[ks] - r0 : 256;  // MMA N <= 256
+                  const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, nrow);
+                  const uint32_t dcol = tmem + t * 256 + r0;
+                  const uint64_t bd = sdesc(kc + 32 * r0);
+                  mma<BF16>(dcol, ad, bd, id, ks == 0 ? acc : 1u);
+                  if constexpr (BF16) {
+                    mma<BF16>(dcol, ad, sdesc(kc + 32 * G.Nks[ks] + 32 * r0), id, 1u);  // hi x lo
+                    mma<BF16>(dcol, sdesc(as + TC_SLICE), bd, id, 1u);                  // lo x hi
+                  }
                 }
               }
             }
             if (++j == R.kps || ks == G.KS - 1) {
-              mma_commit(empty0 + 8 * slot);  // the slot is free once these MMAs have read it
+              mma_commit(empty0 + 8 * slot);  // the slot is free once both issuers' MMAs have read it
               n++;
               j = 0;
               if (++slot == R.nslots) {
@@ -496,9 +527,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             }
           }
         }
-        acc = 1u;
+        if (O >= 0) acc = 1u;
+        O = On;
       }
-      counts[1] = n;
+      counts[1 + t] = n;
       mma_commit(smem_u32(done));  // arrives when every MMA issued above has completed
     }
     __syncwarp();
@@ -513,18 +545,23 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     }
     tc_fence_after();
     if (ok && !*abort_flag) {
-      const float inv = (float)(1.0 / (4.0 * M_PI * ldexp(side, -level[T])));
       const int b = sb * TC_M + q * 32 + lane;
-      float* Lt = L + (int64_t)T * nc * B + b;
 #pragma unroll
-      for (int c0 = 0; c0 < G.ncp; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-        if (b < B) {
+      for (int t = 0; t < NT; t++) {
+        const int32_t T = gtarget[grp * NT + t];
+        if (T < 0) continue;
+        const float inv = (float)(1.0 / (4.0 * M_PI * ldexp(side, -level[T])));
+        float* Lt = L + (int64_t)T * nc * B + b;
 #pragma unroll
-          for (int i = 0; i < 16; i++) {
-            const int m = c0 + i;
-            if (m < G.nc) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
+        for (int c0 = 0; c0 < G.ncp; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256 + c0), r);
+          if (b < B) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+              const int m = c0 + i;
+              if (m < G.nc) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
+            }
           }
         }
       }
@@ -532,14 +569,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   }
   __syncthreads();
   if (tid == 0 && *abort_flag) {
-    // copies issued but never consumed still land in the ring: wait for them
-    for (int it = counts[1]; it < counts[0]; it++)
+    // copies issued but not consumed by both issuers still land in the ring: wait for them
+    const int consumed = NT == 1 ? counts[1] : min(counts[1], counts[2]);
+    for (int it = consumed; it < counts[0]; it++)
       mbar_wait(full0 + 8 * (it % R.nslots), (uint32_t)((it / R.nslots) & 1), nullptr);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 2)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -560,28 +598,42 @@ struct KeyHash {
 
 TcLayout layout_of(const Plan& P) { return tc_layout(P.p, P.opt.precision == DEMAG_MIXED_BF16X3); }
 
-template <int PP, bool BF16>
+template <int PP, bool BF16, int NT>
 void launch_fixed(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
   static size_t attr = 0;
   const size_t smem = ring_smem(R);
   if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
   const int nsb = (B + TC_M - 1) / TC_M;
-  dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)nsb);
-  k_m2l_tc<PP, BF16><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.m2l_op, P.cell_level,
-                                                    P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+  if (NT == 1) {
+    dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)nsb);
+    k_m2l_tc<PP, BF16, NT><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.tc_g1_off, P.m2l_src, P.m2l_op,
+                                                          P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+  } else {
+    dim3 grid((unsigned)P.tc_n_g2, (unsigned)nsb);
+    k_m2l_tc<PP, BF16, NT><<<grid, TC_THREADS, smem, s>>>(P.tc_g2_tgt, P.tc_g2_off, P.tc_g2_src, P.tc_g2_op,
+                                                          P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+  }
   DM_LAUNCH("k_m2l_tc");
+}
+
+template <int PP, bool BF16>
+void launch_nt(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
+  if constexpr (tc_layout(PP, BF16).tmem_cols <= 256) {
+    if (R.nt == 2) return launch_fixed<PP, BF16, 2>(P, R, B, QP, L, err, s);
+  }
+  launch_fixed<PP, BF16, 1>(P, R, B, QP, L, err, s);
 }
 
 template <bool BF16>
 void launch_order(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
   switch (P.p) {
-    case 4: launch_fixed<4, BF16>(P, R, B, QP, L, err, s); break;
-    case 6: launch_fixed<6, BF16>(P, R, B, QP, L, err, s); break;
-    case 8: launch_fixed<8, BF16>(P, R, B, QP, L, err, s); break;
-    case 10: launch_fixed<10, BF16>(P, R, B, QP, L, err, s); break;
+    case 4: launch_nt<4, BF16>(P, R, B, QP, L, err, s); break;
+    case 6: launch_nt<6, BF16>(P, R, B, QP, L, err, s); break;
+    case 8: launch_nt<8, BF16>(P, R, B, QP, L, err, s); break;
+    case 10: launch_nt<10, BF16>(P, R, B, QP, L, err, s); break;
     default: fail(DEMAG_ERR_UNSUPPORTED, "no tensor-core M2L for this order");
   }
 }
@@ -597,15 +649,19 @@ void launch_main(Plan& P, const TcRing& R, int B, const unsigned char* QP, float
 // fits), ~200 KB gives one CTA the whole shared memory
 constexpr int TC_BUDGET_2 = 100 * 1024, TC_BUDGET_1 = 200 * 1024;
 
-// default ring shape: two CTAs per SM, ~32 KB slots
-void default_ring(const TcLayout& G, TcRing& R) {
-  const int budget = G.tmem_cols <= 256 ? TC_BUDGET_2 : TC_BUDGET_1;
-  int kps = std::max(1, std::min(G.KS, (32 * 1024) / G.a_bytes / 2));
-  while (kps > 1 && !make_ring(G, kps, budget, R)) kps--;
-  if (!make_ring(G, kps, budget, R)) make_ring(G, 1, TC_BUDGET_1, R);
+// default launch shape (the fastest measured on GB300 for a ball of 224k tets
+// at p = 8): one target per CTA, 2 k-steps per slot, and a ring small enough
+// for two CTAs per SM when their tensor memory fits; nt / kps override it
+void default_ring(const TcLayout& G, int nt, int kps, TcRing& R) {
+  if (nt == 0) nt = 1;
+  if (kps == 0) kps = std::min(G.KS, 2);
+  const int budget = (nt == 1 && G.tmem_cols <= 256) ? TC_BUDGET_2 : TC_BUDGET_1;
+  for (; kps >= 1; kps--)
+    if (make_ring(G, nt, kps, budget, R) || make_ring(G, nt, kps, TC_BUDGET_1, R)) return;
+  R.nslots = 0;
 }
 
-// autotune: time every ring shape on the plan's own lists (zero moments,
+// autotune: time every launch shape on the plan's own lists (zero moments,
 // 128 states) and keep the fastest
 void tune_ring(Plan& P, const TcLayout& G) {
   cudaStream_t s = P.stream;
@@ -619,26 +675,28 @@ void tune_ring(Plan& P, const TcLayout& G) {
   DM_CUDA(cudaEventCreate(&a));
   DM_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
-  for (int budget : {TC_BUDGET_2, TC_BUDGET_1}) {
-    if (budget == TC_BUDGET_2 && G.tmem_cols > 256) continue;
-    for (int kps = 1; kps <= std::min(G.KS, 8); kps++) {
-      TcRing R;
-      if (!make_ring(G, kps, budget, R)) continue;
-      if (R.nslots < 2 || ring_smem(R) > 227 * 1024) continue;
-      launch_main(P, R, B, qp.p, L.p, err.p, s);  // warm-up
-      DM_CUDA(cudaEventRecord(a, s));
-      launch_main(P, R, B, qp.p, L.p, err.p, s);
-      DM_CUDA(cudaEventRecord(b, s));
-      DM_CUDA(cudaEventSynchronize(b));
-      float ms = 0.f;
-      DM_CUDA(cudaEventElapsedTime(&ms, a, b));
-      if (ms < best) {
-        best = ms;
-        P.tc_kps = kps;
-        P.tc_budget = budget;
+  for (int nt = 1; nt <= 2; nt++)
+    for (int budget : {TC_BUDGET_2, TC_BUDGET_1}) {
+      if (budget == TC_BUDGET_2 && (nt == 2 || G.tmem_cols > 256)) continue;  // one CTA per SM anyway
+      for (int kps = 1; kps <= std::min(G.KS, 8); kps++) {
+        TcRing R;
+        if (!make_ring(G, nt, kps, budget, R)) continue;
+        if (ring_smem(R) > 227 * 1024) continue;
+        launch_main(P, R, B, qp.p, L.p, err.p, s);  // warm-up
+        DM_CUDA(cudaEventRecord(a, s));
+        launch_main(P, R, B, qp.p, L.p, err.p, s);
+        DM_CUDA(cudaEventRecord(b, s));
+        DM_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        DM_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+          best = ms;
+          P.tc_nt = nt;
+          P.tc_kps = kps;
+          P.tc_budget = budget;
+        }
       }
     }
-  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   int h_err = 0;
@@ -647,8 +705,8 @@ void tune_ring(Plan& P, const TcLayout& G) {
 }
 
 bool current_ring(const Plan& P, const TcLayout& G, TcRing& R) {
-  if (P.tc_kps > 0 && make_ring(G, P.tc_kps, P.tc_budget, R)) return true;
-  default_ring(G, R);
+  if (P.tc_kps > 0 && make_ring(G, P.tc_nt, P.tc_kps, P.tc_budget, R)) return true;
+  default_ring(G, P.opt.m2l_targets_per_cta, P.opt.m2l_kps, R);
   return R.nslots >= 2;
 }
 
@@ -713,11 +771,52 @@ void build_m2l_tc(Plan& P) {
     build_ops<true>(P, G, keys);
   else
     build_ops<false>(P, G, keys);
+  // groups of one target: the target's own list
+  const int64_t nT = (int64_t)P.h_m2l_targets.size();
+  std::vector<int64_t> g1(nT + 1);
+  for (int64_t i = 0; i < nT; i++) g1[i] = off[P.h_m2l_targets[i]];
+  g1[nT] = nT ? off[P.h_m2l_targets[nT - 1] + 1] : 0;
+  P.tc_g1_off = dalloc<int64_t>(P, nT + 1);
+  DM_CUDA(cudaMemcpyAsync(P.tc_g1_off, g1.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  // groups of two consecutive targets: the union of their (ascending) lists
+  if (G.tmem_cols <= 256) {
+    const int64_t ng = (nT + 1) / 2;
+    std::vector<int32_t> tgt(2 * ng, -1), usrc, uop;
+    std::vector<int64_t> uoff(ng + 1, 0);
+    usrc.reserve(P.n_m2l);
+    uop.reserve(2 * P.n_m2l);
+    for (int64_t g = 0; g < ng; g++) {
+      const int32_t T0 = P.h_m2l_targets[2 * g], T1 = 2 * g + 1 < nT ? P.h_m2l_targets[2 * g + 1] : -1;
+      tgt[2 * g] = T0;
+      tgt[2 * g + 1] = T1;
+      int64_t i = off[T0], ie = off[T0 + 1], j = T1 >= 0 ? off[T1] : 0, je = T1 >= 0 ? off[T1 + 1] : 0;
+      while (i < ie || j < je) {
+        const int32_t si = i < ie ? src[i] : INT32_MAX, sj = j < je ? src[j] : INT32_MAX;
+        const int32_t sm = std::min(si, sj);
+        usrc.push_back(sm);
+        uop.push_back(si == sm ? op[i++] : -1);
+        uop.push_back(sj == sm ? op[j++] : -1);
+      }
+      uoff[g + 1] = (int64_t)usrc.size();
+    }
+    P.tc_n_g2 = ng;
+    P.tc_g2_tgt = dalloc<int32_t>(P, 2 * ng);
+    P.tc_g2_off = dalloc<int64_t>(P, ng + 1);
+    P.tc_g2_src = dalloc<int32_t>(P, usrc.size());
+    P.tc_g2_op = dalloc<int32_t>(P, uop.size());
+    DM_CUDA(cudaMemcpyAsync(P.tc_g2_tgt, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.tc_g2_off, uoff.data(), uoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.tc_g2_src, usrc.data(), usrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.tc_g2_op, uop.data(), uop.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  DM_CUDA(cudaStreamSynchronize(s));
+  P.tc_nt = 1;
   P.tc_kps = 0;
   P.tc_budget = 0;
-  if (P.opt.autotune) tune_ring(P, G);
+  if (P.opt.autotune && P.opt.m2l_targets_per_cta == 0 && P.opt.m2l_kps == 0) tune_ring(P, G);
   TcRing R;
   if (!current_ring(P, G, R)) fail(DEMAG_ERR_UNSUPPORTED, "no ring shape fits the tensor-core M2L");
+  P.tc_nt = R.nt;
   P.tc_kps = R.kps;
   P.tc_budget = R.nslots * R.slot_bytes;
 }

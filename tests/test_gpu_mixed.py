@@ -150,3 +150,25 @@ def test_tensor_core_ring_shape_does_not_change_results():
     ua, Ha = a.eval(M)
     ub, Hb = b.eval(M)
     assert torch.equal(ua, ub) and torch.equal(Ha, Hb)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_tensor_core_two_target_groups_match_one_target(prec):
+    """Two targets per CTA over the union of their source lists (each source's
+    moments loaded once) must give bit-identical L to one target per CTA: the
+    MMA sequence of every target is the same, sources absent from a target's
+    list only skip its MMAs."""
+    from paper_1606_00247_gb300 import _lib as L
+
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=128)
+    a = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1, precision=prec, m2l_targets_per_cta=2)
+    assert a.stats()["m2l_targets_per_cta"] == 2
+    ua, Ha = a.eval(M)
+    b = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1, precision=prec, m2l_targets_per_cta=1,
+              m2l_kps=3)
+    assert b.stats()["m2l_targets_per_cta"] == 1 and b.stats()["m2l_kps"] == 3
+    ub, Hb = b.eval(M)
+    assert torch.equal(ua, ub) and torch.equal(Ha, Hb)
+    u64, _ = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1).eval(M)
+    assert per_state(ua.cpu().numpy(), u64.cpu().numpy()) <= (1e-4 if prec == "bf16x3" else 1e-3)
