@@ -185,6 +185,15 @@ def alu_peak_tflops(kind, sm_mhz):
     return lanes / 1e12 if kind == "fp32" else lanes / 64 / 1e12
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from one `ncu --set full` capture on GB300 of this exact
+# configuration and kernel version; any other configuration reports null
+NCU_TRAFFIC = {
+    # (stage, precision, p, leaf, batch, n_tets, targets per CTA, kps): bytes
+    ("m2l", "bf16x3", 8, 128, 128, 223668, 1, 2): 25.835e9 + 0.244e9,
+}
+
+
 def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
     """Roofline of the dominant stage from its live per-stage CUDA-event time."""
     ms = stats["stage_ms"]
@@ -215,8 +224,10 @@ def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
         base = sus if sus else peaks.get("bf16_tflops", 1900.0)
         peak = base * (1.1 / 2.25) if precision == "tf32" else base
         tile_flops = m2l_tile_flops(p, precision) * stats["n_m2l"] * B / launches_per_eval
+        key = ("m2l", precision, p, stats["leaf_size"], B, stats["n_tets"], stats.get("m2l_targets_per_cta"),
+               stats.get("m2l_kps"))
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(key),
                     "executed_tflops": tile_flops / per_launch_s / 1e12,
                     "peak_source": ("measured bf16 sustained (MEASURED_PEAKS.json)" if sus else
                                     "measured bf16 burst (MEASURED_PEAKS.json)")
@@ -366,11 +377,26 @@ def run_ours(args, rank, world, local_rank):
         t64 = ev0.elapsed_time(ev1) / 2
         eu = max(float(torch.linalg.norm(u[k] - u64[k]) / torch.linalg.norm(u64[k])) for k in range(nref))
         eh = max(float(torch.linalg.norm(H[k] - H64[k]) / torch.linalg.norm(H64[k])) for k in range(nref))
+        p64.close()
+        # the FP64 path batched as well (its M2L is bound by the FP64 pipe, so a
+        # moderate batch already reaches its throughput)
+        nb = min(B, 16)
+        p64b = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64",
+                    near_mode=1, max_batch=nb, device=dev)
+        p64b.eval(M[:nb])
+        ev0.record(stream)
+        for _ in range(2):
+            p64b.eval(M[:nb])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64b = ev0.elapsed_time(ev1) / 2
+        p64b.close()
         ref_info = {"fp64_gpu_fmm_evals_per_s": 1e3 / t64, "fp64_ms_per_eval": t64, "fp64_near_mode": 1,
+                    "fp64_batched_evals_per_s": nb * 1e3 / t64b, "fp64_batch": nb,
                     "rel_l2_u_vs_fp64": eu, "rel_l2_H_vs_fp64": eh, "states_checked": nref,
                     "meets_1e-4": bool(eu <= 1e-4 and eh <= 1e-4),
-                    "speedup_vs_fp64_gpu_fmm": value / (1e3 / t64)}
-        p64.close()
+                    "speedup_vs_fp64_gpu_fmm": value / (1e3 / t64),
+                    "speedup_vs_fp64_batched": value / (nb * 1e3 / t64b)}
 
     if rank != 0:
         return None
