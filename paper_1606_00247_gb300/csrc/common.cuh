@@ -184,6 +184,8 @@ struct Plan {
   TEnt* m2m_ent = nullptr;
   int32_t* l2l_eoff = nullptr;      // nc + 1
   TEnt* l2l_ent = nullptr;
+  int32_t* par_list = nullptr;      // cells with children, level by level
+  std::vector<int64_t> par_start;   // host, nlevels + 1: parents of level l are par_list[par_start[l] ..]
   // FP32 mass-lumped gradient operator (mixed precision), rows by sorted node:
   //   H_i = sum_e w_e u_{col_e},  w_e = -(1/V_i) sum_{t ni i, col_e} vol_t grad lambda_{col_e}^t
   int64_t* hg_off = nullptr;        // nn + 1

@@ -140,16 +140,15 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
 
 // M2M of one level: thread per (cell, n, state); the warp shares (cell, n), so
 // the coefficient list is read as a broadcast and the child moments coalesce
-__global__ void k_m2m32(int64_t lb, int64_t ncl, const int32_t* __restrict__ child0, const int32_t* __restrict__ nchild,
-                        const uint64_t* __restrict__ prefix, const int32_t* __restrict__ eoff,
-                        const TEnt* __restrict__ ent, int nc, int B, float* Q) {
+__global__ void k_m2m32(const int32_t* __restrict__ parents, int64_t npar, const int32_t* __restrict__ child0,
+                        const int32_t* __restrict__ nchild, const uint64_t* __restrict__ prefix,
+                        const int32_t* __restrict__ eoff, const TEnt* __restrict__ ent, int nc, int B, float* Q) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)nc * B;
-  if (idx >= ncl * per) return;
-  const int64_t P = lb + idx / per;
+  if (idx >= npar * per) return;
+  const int64_t P = parents[idx / per];
   const int rem = (int)(idx % per), n = rem / B, b = rem - n * B;
   const int nch = nchild[P];
-  if (nch == 0) return;
   const int32_t c0 = child0[P];
   const int e0 = eoff[n], e1 = eoff[n + 1];
   float acc = 0.f;
@@ -239,16 +238,16 @@ __global__ void k_m2l32(const int32_t* __restrict__ targets, const int64_t* __re
 // L2L from the parents of one level: thread per (parent, m, state) feeding all
 // children at once (each parent coefficient is loaded once; the octant only
 // flips signs); added to the children's own M2L results
-__global__ void k_l2l32(int64_t lb, int64_t ncl, const int32_t* __restrict__ child0,
+__global__ void k_l2l32(const int32_t* __restrict__ parents, int64_t npar, const int32_t* __restrict__ child0,
                         const int32_t* __restrict__ nchild, const int4* __restrict__ range,
                         const uint64_t* __restrict__ prefix, const int32_t* __restrict__ eoff,
                         const TEnt* __restrict__ ent, int nc, int B, float* L) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)nc * B;
-  if (idx >= ncl * per) return;
-  const int64_t P = lb + idx / per;
+  if (idx >= npar * per) return;
+  const int64_t P = parents[idx / per];
   const int nch = nchild[P];
-  if (nch == 0) return;
+  if (range[P].w == range[P].z) return;  // no target node below this cell
   const int rem = (int)(idx % per), m = rem / B, b = rem - m * B;
   const int32_t c0 = child0[P];
   int oct[8];
@@ -273,39 +272,38 @@ __global__ void k_l2l32(int64_t lb, int64_t ncl, const int32_t* __restrict__ chi
     }
 }
 
-// L2P: thread per (node, state); u = sum_m Lt_m s_m(z/s) over the node's leaf
-__global__ void k_l2p32(int64_t nn, const int32_t* __restrict__ node_leaf, const int32_t* __restrict__ level,
-                        const double* __restrict__ nodes_s, const double* __restrict__ centre, double side, int p,
-                        int nc, int B, const float* __restrict__ L, float* u) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= nn * B) return;
-  const int64_t i = idx / B;
-  const int b = (int)(idx - i * B);
+// L2P: block per (node, 128 states); the node's monomials s_m(z/s) are formed
+// once in shared memory, then thread = state: u = sum_m Lt_m s_m (coalesced L)
+__global__ void __launch_bounds__(128) k_l2p32(const int32_t* __restrict__ node_leaf, const int32_t* __restrict__ level,
+                                               const double* __restrict__ nodes_s, const double* __restrict__ centre,
+                                               double side, int nc, int B, const float* __restrict__ L, float* u) {
+  __shared__ float sm_[MAX_NCOEF];
+  const int64_t i = blockIdx.x;
   const int32_t c = node_leaf[i];
   const double inv_s = 1.0 / ldexp(side, -level[c]);
-  float px[MAX_P + 1], py[MAX_P + 1], pz[MAX_P + 1];
-  const float zx = (float)((nodes_s[3 * i] - centre[3 * c]) * inv_s),
-              zy = (float)((nodes_s[3 * i + 1] - centre[3 * c + 1]) * inv_s),
-              zz = (float)((nodes_s[3 * i + 2] - centre[3 * c + 2]) * inv_s);
-  px[0] = py[0] = pz[0] = 1.f;
-#pragma unroll
-  for (int e = 1; e <= MAX_P; e++) {
-    px[e] = px[e - 1] * zx / e;
-    py[e] = py[e - 1] * zy / e;
-    pz[e] = pz[e - 1] * zz / e;
+  const float z[3] = {(float)((nodes_s[3 * i] - centre[3 * c]) * inv_s),
+                      (float)((nodes_s[3 * i + 1] - centre[3 * c + 1]) * inv_s),
+                      (float)((nodes_s[3 * i + 2] - centre[3 * c + 2]) * inv_s)};
+  for (int m = threadIdx.x; m < nc; m += blockDim.x) {
+    int e[3];
+    mi_decode(m, e[0], e[1], e[2]);
+    float v = 1.f;
+    for (int a = 0; a < 3; a++)
+      for (int k = 1; k <= e[a]; k++) v = v * z[a] / k;
+    sm_[m] = v;
   }
+  __syncthreads();
+  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= B) return;
   const float* Lc = L + (int64_t)c * nc * B + b;
-  float v = 0.f;
+  float v0 = 0.f, v1 = 0.f;
   int m = 0;
-#pragma unroll
-  for (int t = 0; t <= MAX_P; t++) {
-    if (t > p) break;
-#pragma unroll
-    for (int j = 0; j <= t; j++)
-#pragma unroll
-      for (int mz = 0; mz <= j; mz++, m++) v = fmaf(Lc[(int64_t)m * B], px[t - j] * py[j - mz] * pz[mz], v);
+  for (; m + 1 < nc; m += 2) {
+    v0 = fmaf(Lc[(int64_t)m * B], sm_[m], v0);
+    v1 = fmaf(Lc[(int64_t)(m + 1) * B], sm_[m + 1], v1);
   }
-  u[i * B + b] = v;
+  if (m < nc) v0 = fmaf(Lc[(int64_t)m * B], sm_[m], v0);
+  u[i * B + b] = v0 + v1;
 }
 
 // u and the mass-lumped H of the mixed path, in the caller's layout: tiles of
@@ -475,9 +473,28 @@ static void build_gradient_operator(Plan& P) {
   DM_CUDA(cudaStreamSynchronize(s));
 }
 
+// cells with children, level by level (the M2M and L2L launches run over these only)
+static void build_parent_lists(Plan& P) {
+  cudaStream_t s = P.stream;
+  std::vector<int32_t> nch(P.ncells), list;
+  DM_CUDA(cudaMemcpyAsync(nch.data(), P.cell_nchild, sizeof(int32_t) * P.ncells, cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  P.par_start.assign(1, 0);
+  for (int l = 0; l < P.nlevels; l++) {
+    for (int64_t c = P.level_start[l]; c < P.level_start[l + 1]; c++)
+      if (nch[c] > 0) list.push_back((int32_t)c);
+    P.par_start.push_back((int64_t)list.size());
+  }
+  P.par_list = dalloc<int32_t>(P, std::max<size_t>(list.size(), 1));
+  if (!list.empty())
+    DM_CUDA(cudaMemcpyAsync(P.par_list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_mixed_operators(Plan& P) {
   build_translations(P);
   build_gradient_operator(P);
+  build_parent_lists(P);
   cudaStream_t s = P.stream;
   P.Ghat32 = dalloc<float>(P, std::max<int64_t>(P.n_sup, 1) * P.nc1);
   if (!P.h_src_leaves.empty()) {
@@ -517,9 +534,10 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.end();
   clk.begin(DEMAG_STAGE_M2M);
   for (int l = P.nlevels - 2; l >= 0; l--) {
-    int64_t lb = P.level_start[l], le = P.level_start[l + 1];
-    k_m2m32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_child0, P.cell_nchild, P.cell_prefix,
-                                                          P.m2m_eoff, P.m2m_ent, nc, B, W.Q32);
+    const int64_t pb = P.par_start[l], np = P.par_start[l + 1] - pb;
+    if (np == 0) continue;
+    k_m2m32<<<nblk(np * nc * B, 256), 256, 0, s>>>(P.par_list + pb, np, P.cell_child0, P.cell_nchild, P.cell_prefix,
+                                                   P.m2m_eoff, P.m2m_ent, nc, B, W.Q32);
     DM_LAUNCH("k_m2m32");
     clk.launched();
   }
@@ -542,16 +560,17 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.end();
   clk.begin(DEMAG_STAGE_L2L);
   for (int l = 0; l + 1 < P.nlevels; l++) {  // parents at level l, children at l + 1
-    int64_t lb = P.level_start[l], le = P.level_start[l + 1];
-    k_l2l32<<<nblk((le - lb) * nc * B, 256), 256, 0, s>>>(lb, le - lb, P.cell_child0, P.cell_nchild, P.cell_range,
-                                                          P.cell_prefix, P.l2l_eoff, P.l2l_ent, nc, B, W.L32);
+    const int64_t pb = P.par_start[l], np = P.par_start[l + 1] - pb;
+    if (np == 0) continue;
+    k_l2l32<<<nblk(np * nc * B, 256), 256, 0, s>>>(P.par_list + pb, np, P.cell_child0, P.cell_nchild, P.cell_range,
+                                                   P.cell_prefix, P.l2l_eoff, P.l2l_ent, nc, B, W.L32);
     DM_LAUNCH("k_l2l32");
     clk.launched();
   }
   clk.end();
   clk.begin(DEMAG_STAGE_L2P);
-  k_l2p32<<<nblk(P.nn * B, 256), 256, 0, s>>>(P.nn, P.node_leaf, P.cell_level, P.nodes_s, P.cell_centre, P.side, p,
-                                              nc, B, W.L32, W.u32);
+  k_l2p32<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.node_leaf, P.cell_level, P.nodes_s,
+                                                                             P.cell_centre, P.side, nc, B, W.L32, W.u32);
   DM_LAUNCH("k_l2p32");
   clk.launched();
   clk.end();
