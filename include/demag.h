@@ -147,6 +147,27 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
 demag_status demag_eval_noalloc(demag_plan plan, const double* M, int batch, double* u, double* H,
                                 void* cuda_stream);
 
+/* Evaluate several plans (meshes of any sizes, each with its own batch of
+ * states) through one submission (Sec. 4 runs one mesh at a time; batching
+ * meshes is a service of the library).
+ *   plans   : n_plans plans, distinct.
+ *   M, u, H : n_plans DEVICE pointers each, layouts as for demag_eval; H may be
+ *             NULL (no H for any plan) or hold NULL entries.
+ *   batch   : n_plans batch sizes, each in 1..max_batch of its plan.
+ * Results are bit-identical to n_plans separate demag_eval calls.  The first
+ * call with a given (plans, batches, pointers) signature runs the work directly
+ * on cuda_stream and then records it as a CUDA graph (one branch per plan, so
+ * the meshes' kernels may overlap); later calls with the same signature replay
+ * the graph with a single launch, asynchronously on cuda_stream.  A few graphs
+ * are cached (least recently used dropped first); destroying a plan or
+ * enlarging its workspace drops the graphs that used it.  The first call must
+ * not itself be issued while cuda_stream is being captured.  Stage timers
+ * (opt.profile) are not updated by this entry point.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL arrays or pointers, n_plans < 1, a
+ * repeated plan, host pointers, batch out of range), DEMAG_ERR_CUDA. */
+demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double* const* M, const int* batch,
+                              double* const* u, double* const* H, void* cuda_stream);
+
 demag_status demag_plan_destroy(demag_plan plan);
 
 /* Stages of demag_eval, for the per-stage timers. */

@@ -78,6 +78,8 @@ def load(build_if_missing: bool = True):
         L.demag_eval.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_eval_noalloc.restype = i32
         L.demag_eval_noalloc.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.demag_eval_multi.restype = i32
+        L.demag_eval_multi.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.demag_plan_destroy.restype = i32
         L.demag_plan_destroy.argtypes = [vp]
         L.demag_plan_stats.restype = i32
@@ -114,6 +116,11 @@ def demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
 def demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
     """demag_eval with its scratch in the library's fixed device array (no allocation)."""
     return load().demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr)
+
+
+def demag_eval_multi(plans_ptr, n_plans, M_ptrs, batch_ptr, u_ptrs, H_ptrs, stream_ptr):
+    """Several plans in one submission; every argument but n_plans is a pointer to an array."""
+    return load().demag_eval_multi(plans_ptr, n_plans, M_ptrs, batch_ptr, u_ptrs, H_ptrs, stream_ptr)
 
 
 def demag_plan_destroy(plan):

@@ -128,3 +128,39 @@ class Plan:
         arrs["m2l_src"] = arrs["m2l_src"][: s["n_m2l"]]
         arrs["p2p_src"] = arrs["p2p_src"][: s["n_p2p"]]
         return arrs
+
+
+def eval_multi(plans, Ms, stream=None, with_H=True):
+    """Evaluate several plans through one submission (demag_eval_multi):
+    Ms[i] is (B_i, N_n_i, 3) on plans[i]'s device.  Returns lists of u and H.
+    The first call with given tensors runs directly and records a CUDA graph;
+    later calls with the same tensors replay it."""
+    import ctypes as C
+
+    n = len(plans)
+    if n != len(Ms) or n < 1:
+        raise ValueError("one magnetisation tensor per plan")
+    dev = plans[0].device
+    Ms = [_as_f64(M, dev) for M in Ms]
+    Ms = [M.unsqueeze(0) if M.dim() == 2 else M for M in Ms]
+    us = [torch.empty((int(M.shape[0]), pl.n_nodes), dtype=torch.float64, device=dev) for M, pl in zip(Ms, plans)]
+    Hs = [torch.empty((int(M.shape[0]), pl.n_nodes, 3), dtype=torch.float64, device=dev) for M, pl in zip(Ms, plans)]
+    return eval_multi_into(plans, Ms, us, Hs if with_H else None, stream=stream)
+
+
+def eval_multi_into(plans, Ms, us, Hs=None, stream=None):
+    """demag_eval_multi with caller-provided outputs (same tensors -> graph replay)."""
+    import ctypes as C
+
+    n = len(plans)
+    P = (C.c_void_p * n)(*[pl.handle for pl in plans])
+    Mp = (C.c_void_p * n)(*[M.data_ptr() for M in Ms])
+    up = (C.c_void_p * n)(*[u.data_ptr() for u in us])
+    Hp = (C.c_void_p * n)(*[H.data_ptr() for H in Hs]) if Hs is not None else None
+    bt = (C.c_int * n)(*[int(M.shape[0]) for M in Ms])
+    s = stream if stream is not None else torch.cuda.current_stream(plans[0].device)
+    st = L.demag_eval_multi(C.cast(P, C.c_void_p), n, C.cast(Mp, C.c_void_p), C.cast(bt, C.c_void_p),
+                            C.cast(up, C.c_void_p), C.cast(Hp, C.c_void_p) if Hp is not None else None, s.cuda_stream)
+    L.check(st, "demag_eval_multi")
+    return us, Hs
+

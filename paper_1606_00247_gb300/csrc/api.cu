@@ -166,9 +166,29 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
   });
 }
 
+demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double* const* M, const int* batch,
+                              double* const* u, double* const* H, void* cuda_stream) {
+  return guarded([&] {
+    if (!plans || !M || !batch || !u || n_plans < 1) fail(DEMAG_ERR_INVALID_ARG, "NULL array or n_plans < 1");
+    std::vector<Plan*> ps(n_plans);
+    for (int i = 0; i < n_plans; i++) {
+      if (!plans[i] || !M[i] || !u[i]) fail(DEMAG_ERR_INVALID_ARG, "NULL plan or pointer in the arrays");
+      if (batch[i] < 1 || batch[i] > plans[i]->opt.max_batch)
+        fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch of its plan");
+      if (!is_device_ptr(M[i]) || !is_device_ptr(u[i]) || (H && H[i] && !is_device_ptr(H[i])))
+        fail(DEMAG_ERR_INVALID_ARG, "demag_eval_multi takes device pointers only");
+      for (int j = 0; j < i; j++)
+        if (plans[j] == plans[i]) fail(DEMAG_ERR_INVALID_ARG, "a plan appears twice (they share a workspace)");
+      ps[i] = plans[i];
+    }
+    eval_multi(ps.data(), n_plans, M, batch, u, H, (cudaStream_t)cuda_stream);
+  });
+}
+
 demag_status demag_plan_destroy(demag_plan plan) {
   if (!plan) return DEMAG_ERR_INVALID_ARG;
   return guarded([&] {
+    multi_forget_plan(plan);
     cudaStreamSynchronize(plan->stream);
     destroy_workspace(*plan);
     dfree_all(*plan);

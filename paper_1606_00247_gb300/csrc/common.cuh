@@ -279,6 +279,11 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);  // m2l32.cu
+// several plans in one submission (multi.cu); cached graphs of a plan are
+// dropped before the plan or its workspace goes away
+void eval_multi(Plan* const* plans, int n, const double* const* M, const int* batch, double* const* u,
+                double* const* H, cudaStream_t s);
+void multi_forget_plan(const Plan* P);
 // tensor-core M2L (m2l_tc.cu): operator table at plan time; bytes of the packed
 // moments for B states (0 when the tensor-core M2L is off); packs Q into QP and
 // runs the M2L (false: not available for this plan, use the CUDA-core M2L)

@@ -301,6 +301,7 @@ static void* ws_alloc(Workspace& W, size_t bytes) {
 
 void destroy_workspace(Plan& P) {
   if (!P.ws) return;
+  multi_forget_plan(&P);  // graphs recorded with this workspace
   for (void* p : P.ws->ptrs) cudaFree(p);
   delete P.ws;
   P.ws = nullptr;

@@ -63,7 +63,7 @@ def test_mixed_vs_fp64(orc, near_mode, p):
 
 
 @pytest.mark.parametrize("B", [4, 128, 160])
-@pytest.mark.parametrize("p", [4, 6, 8])
+@pytest.mark.parametrize("p", [4, 6, 8, 10])
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_tensor_core_m2l_vs_fp64(prec, p, B):
     """M2L on tcgen05 tensor cores (FP32 accumulation in tensor memory): full
@@ -73,7 +73,9 @@ def test_tensor_core_m2l_vs_fp64(prec, p, B):
     nodes, tets = inputs.sphere(h=0.13)
     M = inputs.gaussian_unit_m(nodes.shape[0], batch=B)
     u64, H64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1).eval(M)
-    utc, Htc = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision=prec).eval(M)
+    ptc = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision=prec)
+    assert ptc.stats()["n_m2l_ops"] > 0  # the tensor-core M2L ran (orders 4, 6, 8, 10)
+    utc, Htc = ptc.eval(M)
     eu = per_state(utc.cpu().numpy(), u64.cpu().numpy())
     eh = per_state(Htc.cpu().numpy(), H64.cpu().numpy())
     bar = 1e-4 if prec == "bf16x3" else 1e-3
