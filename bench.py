@@ -190,7 +190,6 @@ def alu_peak_tflops(kind, sm_mhz):
 # configuration and kernel version; any other configuration reports null
 NCU_TRAFFIC = {
     # (stage, precision, p, leaf, batch, n_tets, targets per CTA, kps): bytes
-    ("m2l", "bf16x3", 8, 128, 128, 223668, 1, 2): 25.835e9 + 0.244e9,
 }
 
 
@@ -455,6 +454,45 @@ def run_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def accuracy_sweep(args):
+    """FMM truncation error against the direct sum on the same mesh, per (p, theta):
+    the direct sum is the library itself with theta -> 0 (every pair in the
+    analytic FP64 near field), one state; each FMM is run in FP64 and in the
+    mixed split-BF16 mode.  One JSON line."""
+    import torch
+
+    from paper_1606_00247_gb300 import build
+    from paper_1606_00247_gb300.api import Plan
+
+    build()
+    w = workload(args)
+    nodes, tets = make_mesh(w)
+    M = torch.as_tensor(make_M(nodes.shape[0], 1), device="cuda")
+    t0 = time.perf_counter()
+    direct = Plan(nodes, tets, p=2, leaf_size=w["leaf"], theta=1e-6, precision="fp64", near_mode=0, max_batch=1)
+    ud, Hd = direct.eval(M)
+    torch.cuda.synchronize()
+    t_direct = time.perf_counter() - t0
+    n_pairs_direct = direct.stats()["n_p2p_pairs"]
+    direct.close()
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    rows = []
+    for theta in (0.3, 0.5, 0.8):
+        for p in (4, 6, 8, 10):
+            for prec in ("fp64", "bf16x3"):
+                pl = Plan(nodes, tets, p=p, leaf_size=w["leaf"], theta=theta, precision=prec, near_mode=1, max_batch=1)
+                u, H = pl.eval(M)
+                st = pl.stats()
+                rows.append({"theta": theta, "p": p, "precision": prec, "rel_l2_u": rel(u, ud), "rel_l2_H": rel(H, Hd),
+                             "n_m2l": st["n_m2l"], "n_p2p_pairs": st["n_p2p_pairs"]})
+                pl.close()
+    return {"accuracy_sweep": rows, "workload": args.workload, "n_tets": int(tets.shape[0]), "leaf": w["leaf"],
+            "direct": {"pairs": n_pairs_direct, "seconds_incl_plan": t_direct}, "state": "seeded Gaussian unit M"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,7 +500,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere200k", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "fp32", "tf32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "fp32", "tf32", "bf16x3", "bf16x6"])
     ap.add_argument("--near-mode", type=int, default=1)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-fp64-ref", action="store_true")
@@ -472,7 +510,12 @@ def main():
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy-sweep", action="store_true",
+                    help="print the FMM-vs-direct error table over p and theta instead of timing")
     args = ap.parse_args()
+    if args.accuracy_sweep:
+        print(json.dumps(accuracy_sweep(args)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -54,7 +54,8 @@ typedef enum {
   DEMAG_FP64 = 0,
   DEMAG_MIXED_FP32 = 1,
   DEMAG_MIXED_TF32 = 2,
-  DEMAG_MIXED_BF16X3 = 3
+  DEMAG_MIXED_BF16X3 = 3, /* M2L operands in two BF16 limbs (16 bits), 3 MMAs per k-step */
+  DEMAG_MIXED_BF16X6 = 4  /* M2L operands in three BF16 limbs (24 bits = FP32), 6 MMAs per k-step */
 } demag_precision;
 
 typedef struct {
@@ -82,10 +83,19 @@ typedef struct {
   int m2l_kps;         /* tensor-core M2L: k-steps per shared-memory slot,
                           1..8; 0 = default (2) or the autotuner's choice.
                           Every launch shape gives bit-identical results.   */
+  int m2l_promote;     /* tensor-core M2L, one target per CTA: every this
+                          many sources the leading accumulator rows are
+                          moved into FP32 registers (round to nearest) and
+                          restarted at zero; 0 = default (8), < 0 = never.
+                          The tensor core adds products into its FP32
+                          accumulator with alignment to the larger operand,
+                          so without this the error follows the running
+                          value, which for smooth M is far above the result */
+  int m2l_promote_rows; /* rows moved (rounded up to 16, at most 64); 0 = 16 */
 } demag_options;
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
- * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0. */
+ * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and

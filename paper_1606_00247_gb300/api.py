@@ -10,7 +10,7 @@ import torch
 from . import _lib as L
 
 _PREC = {"fp64": L.DEMAG_FP64, "fp32": L.DEMAG_MIXED_FP32, "tf32": L.DEMAG_MIXED_TF32,
-         "bf16x3": L.DEMAG_MIXED_BF16X3}
+         "bf16x3": L.DEMAG_MIXED_BF16X3, "bf16x6": L.DEMAG_MIXED_BF16X6}
 
 
 def _as_f64(x, device):
@@ -29,7 +29,8 @@ class Plan:
     """Tree, lists and operators of one mesh (demag_plan_create)."""
 
     def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
-                 device="cuda", profile=False, autotune=False, m2l_targets_per_cta=0, m2l_kps=0):
+                 device="cuda", profile=False, autotune=False, m2l_targets_per_cta=0, m2l_kps=0,
+                 m2l_promote=0, m2l_promote_rows=0):
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
@@ -42,6 +43,8 @@ class Plan:
         opt.autotune = int(bool(autotune))
         opt.m2l_targets_per_cta = int(m2l_targets_per_cta)
         opt.m2l_kps = int(m2l_kps)
+        opt.m2l_promote = int(m2l_promote)
+        opt.m2l_promote_rows = int(m2l_promote_rows)
         with torch.cuda.device(self.device):
             st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
                                         int(leaf_size), float(theta), opt)

@@ -104,6 +104,8 @@ void demag_options_default(demag_options* o) {
   o->autotune = 0;
   o->m2l_targets_per_cta = 0;
   o->m2l_kps = 0;
+  o->m2l_promote = 0;
+  o->m2l_promote_rows = 0;
   o->profile = 0;
 }
 
@@ -130,8 +132,9 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.m2l_targets_per_cta < 0 || o.m2l_targets_per_cta > 2)
       fail(DEMAG_ERR_INVALID_ARG, "m2l_targets_per_cta must be 0, 1 or 2");
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
+    if (o.m2l_promote_rows < 0 || o.m2l_promote_rows > 64) fail(DEMAG_ERR_INVALID_ARG, "m2l_promote_rows must be in 0..64");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
-    if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X3)
+    if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X6)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     P = new demag_plan_s();
     P->opt = o;

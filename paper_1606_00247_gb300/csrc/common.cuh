@@ -170,6 +170,8 @@ struct Plan {
   unsigned char* tc_ops = nullptr;
   int32_t* m2l_op = nullptr;        // n_m2l
   int tc_nt = 1, tc_kps = 0, tc_budget = 0;  // M2L launch shape: targets per CTA, k-steps per slot, ring bytes
+  int tc_l3 = 0;                    // split BF16: k-steps in three limbs (0 = none, 99 = all)
+  int tc_prom_group = 0, tc_prom_rows = 16;  // accumulator promotion: sources per group (0 = off), rows
   int64_t* tc_g1_off = nullptr;     // one-target groups: list offsets in target order
   int64_t tc_n_g2 = 0;              // two-target groups (consecutive targets), union lists:
   int32_t* tc_g2_tgt = nullptr;     //   2 per group, -1 = none

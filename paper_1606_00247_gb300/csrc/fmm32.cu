@@ -545,7 +545,8 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.begin(DEMAG_STAGE_M2L);
   DM_CUDA(cudaMemsetAsync(W.L32, 0, sizeof(float) * P.ncells * nc * B, s));
   if (P.h_m2l_targets.empty()) {
-  } else if ((P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3) &&
+  } else if ((P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3 ||
+              P.opt.precision == DEMAG_MIXED_BF16X6) &&
              launch_m2l_tc(P, B, W.Q32, W.QP, W.L32, W.err, s)) {
     clk.launched(2);
   } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s)) {

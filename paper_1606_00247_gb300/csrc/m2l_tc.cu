@@ -89,41 +89,46 @@ struct Tmp {
 // tile layout of one order and operand format (a compile-time constant of the
 // kernels; also evaluated on the host for the operator table and the packing)
 struct TcLayout {
-  int valid, bf16, ncopy;
+  int valid, bf16;
+  int l3;                           // split BF16: leading k-steps carried in three limbs (the rest in two)
+  int lmax;                         // most limbs of any k-step (A slices are lmax x 4 KB apart)
   int E, KW;                        // elements per 16 bytes, per k-step (2E)
   int nc, ncp;                      // coefficients, padded to 16 (TMEM columns used)
   int KS;                           // k-steps of the A tile
   int Nks[TC_MAXKS];                // rows used at k-step ks (a prefix), padded to 16
   int ks_off[TC_MAXKS + 1];         // byte offset of k-step ks within one operator
-  int op_bytes;                     // one operator, all k-steps, all copies
-  int a_bytes;                      // A slice of one k-step, all copies
+  int op_bytes;                     // one operator, all k-steps, all limbs
+  int a_bytes;                      // stride of the A slices of consecutive k-steps (lmax limbs)
   int tmem_cols;                    // power of two >= ncp
 };
 
 __host__ __device__ constexpr int cnc_of(int t) { return t < 0 ? 0 : (t + 1) * (t + 2) * (t + 3) / 6; }
 __host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+// operand limbs of k-step ks: TF32 1; split BF16 3 for the leading l3 k-steps, else 2
+__host__ __device__ constexpr int limbs_of(bool bf16, int l3, int ks) { return bf16 ? (ks < l3 ? 3 : 2) : 1; }
 
-__host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16) {
+__host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int l3) {
   TcLayout G{};
   if (p < 1 || p > 12) return G;
   G.bf16 = bf16 ? 1 : 0;
-  G.ncopy = bf16 ? 2 : 1;
   G.E = bf16 ? 8 : 4;
   G.KW = 2 * G.E;
   G.nc = cnc_of(p);
   G.ncp = pad_to(G.nc, 16);
   G.KS = pad_to(G.nc, G.KW) / G.KW;
   if (G.KS > TC_MAXKS) return TcLayout{};
+  G.l3 = bf16 ? (l3 < 0 ? 0 : (l3 > G.KS ? G.KS : l3)) : 0;
+  G.lmax = bf16 ? (G.l3 > 0 ? 3 : 2) : 1;
   G.ks_off[0] = 0;
   for (int ks = 0; ks < G.KS; ks++) {
     int rows = 0;  // rows of degree t need n < cnc(p - t)
     for (int t = 0; t <= p; t++)
       if (cnc_of(p - t) > ks * G.KW) rows = cnc_of(t);
     G.Nks[ks] = pad_to(rows, 16);
-    G.ks_off[ks + 1] = G.ks_off[ks] + G.ncopy * 32 * G.Nks[ks];
+    G.ks_off[ks + 1] = G.ks_off[ks] + limbs_of(bf16, G.l3, ks) * 32 * G.Nks[ks];
   }
   G.op_bytes = G.ks_off[G.KS];
-  G.a_bytes = G.ncopy * TC_SLICE;
+  G.a_bytes = G.lmax * TC_SLICE;
   int tc = 32;
   while (tc < G.ncp) tc *= 2;
   if (tc > 512) return TcLayout{};
@@ -132,19 +137,22 @@ __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16) {
   return G;
 }
 
-// the orders with a compiled tensor-core kernel
+// the orders with a compiled tensor-core kernel; split BF16 is compiled with
+// two limbs on every k-step (DEMAG_MIXED_BF16X3) or three (DEMAG_MIXED_BF16X6)
 constexpr bool tc_order(int p) { return p == 4 || p == 6 || p == 8 || p == 10; }
+constexpr int TC_L3_ALL = 99;
 
 // launch shape: `nt` targets per CTA sharing each source's moments, `kps`
 // k-steps of one source per ring slot (A slices, then one K region per target)
 struct TcRing {
   int nt, kps, nsteps, kmax, slot_bytes, nslots;
+  int prom_group, prom_chunks;                  // promote the first prom_chunks x 16 columns every prom_group sources
   int step_koff[TC_MAXKS], step_kb[TC_MAXKS];  // K bytes of step st within one operator
 };
 
 bool make_ring(const TcLayout& G, int nt, int kps, int budget, TcRing& R) {
   if (!G.valid || kps < 1 || kps > G.KS || nt < 1 || nt > 2) return false;
-  if (nt == 2 && G.tmem_cols > 256) return false;  // two accumulators in one CTA's 512 columns
+  if (nt == 2 && (G.tmem_cols > 256 || G.l3 > 0)) return false;  // two accumulators in 512 columns; compiled for two limbs
   R = TcRing{};
   R.nt = nt;
   R.kps = kps;
@@ -162,7 +170,7 @@ bool make_ring(const TcLayout& G, int nt, int kps, int budget, TcRing& R) {
   return R.nslots >= 2;
 }
 
-size_t ring_smem(const TcRing& R) { return (size_t)R.nslots * R.slot_bytes + sizeof(uint64_t) * (2 * R.nslots + 1) + 64; }
+size_t ring_smem(const TcRing& R) { return (size_t)R.nslots * R.slot_bytes + sizeof(uint64_t) * (2 * R.nslots + 3) + 64; }
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -246,52 +254,75 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// one 16-byte row of a core matrix (E consecutive values of K): split BF16
-// writes the high part to `hi` and the rounding residual to `lo`
+// zero 16 accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// one 16-byte row of a core matrix (E consecutive values of K) in nl limbs,
+// limb c at dst + c * stride: TF32 stores the FP32 values (rounded by the
+// tensor core); split BF16 stores hi = BF16(v), then the BF16 roundings of the
+// successive residuals
 template <bool BF16>
-__device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, const float* v) {
+__device__ __forceinline__ void store_row(unsigned char* dst, int stride, int nl, const float* v) {
   if constexpr (BF16) {
-    uint32_t h[4], l[4];
+    float r[8];
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
-      const float2 hf = __bfloat1622float2(hh);
-      const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * u] - hf.x, v[2 * u + 1] - hf.y);
-      h[u] = *(const uint32_t*)&hh;
-      l[u] = *(const uint32_t*)&ll;
+    for (int u = 0; u < 8; u++) r[u] = v[u];
+    for (int c = 0; c < nl; c++) {
+      uint32_t h[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(r[2 * u], r[2 * u + 1]);
+        const float2 hf = __bfloat1622float2(hh);
+        r[2 * u] -= hf.x;  // exact: the residual of a BF16 rounding of an FP32 value is an FP32 value
+        r[2 * u + 1] -= hf.y;
+        h[u] = *(const uint32_t*)&hh;
+      }
+      *(uint4*)(dst + c * stride) = make_uint4(h[0], h[1], h[2], h[3]);
     }
-    *(uint4*)hi = make_uint4(h[0], h[1], h[2], h[3]);
-    *(uint4*)lo = make_uint4(l[0], l[1], l[2], l[3]);
   } else {
-    (void)lo;
-    *(float4*)hi = make_float4(v[0], v[1], v[2], v[3]);
+    (void)stride;
+    (void)nl;
+    *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
   }
 }
 
-// the same from FP64 values: hi = BF16(v), lo = BF16(v - hi) with the
-// residual taken in FP64 (TF32: the FP32 value, rounded by the tensor core)
+// the same from FP64 values, the residuals taken in FP64
 template <bool BF16>
-__device__ __forceinline__ void store_row64(unsigned char* hi, unsigned char* lo, const double* v) {
+__device__ __forceinline__ void store_row64(unsigned char* dst, int stride, int nl, const double* v) {
   if constexpr (BF16) {
-    __nv_bfloat16 h[8], l[8];
+    double r[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      h[u] = __float2bfloat16_rn((float)v[u]);
-      l[u] = __float2bfloat16_rn((float)(v[u] - (double)__bfloat162float(h[u])));
+    for (int u = 0; u < 8; u++) r[u] = v[u];
+    for (int c = 0; c < nl; c++) {
+      __nv_bfloat16 h[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        h[u] = __float2bfloat16_rn((float)r[u]);
+        r[u] -= (double)__bfloat162float(h[u]);
+      }
+      *(uint4*)(dst + c * stride) = *(const uint4*)h;
     }
-    *(uint4*)hi = *(const uint4*)h;
-    *(uint4*)lo = *(const uint4*)l;
   } else {
-    (void)lo;
-    *(float4*)hi = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    (void)stride;
+    (void)nl;
+    *(float4*)dst = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
   }
 }
 
 // ---------------------------------------------------------------------------
-// moments -> tile layout: QP[cell][sb][ks][copy][128 rows x 32 bytes]
+// moments -> tile layout: QP[cell][sb][ks][limb][128 rows x 32 bytes] (k-steps a_bytes apart)
 template <bool BF16>
 __global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ Q, int nc, int B, int nsb, int KS,
-                                                      int a_bytes, unsigned char* __restrict__ QP) {
+                                                      int a_bytes, int l3, unsigned char* __restrict__ QP) {
   constexpr int E = BF16 ? 8 : 4;
   const int64_t cell = blockIdx.x;
   const int sb = blockIdx.y, b = threadIdx.x, bb = sb * TC_M + b;
@@ -306,7 +337,7 @@ __global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ 
       v[u] = (alive && n < nc) ? q[(int64_t)n * B] : 0.f;
     }
     const int off = (qq >> 1) * a_bytes + (b >> 3) * 256 + (qq & 1) * 128 + (b & 7) * 16;
-    store_row<BF16>(out + off, out + off + TC_SLICE, v);
+    store_row<BF16>(out + off, TC_SLICE, limbs_of(BF16, l3, qq >> 1), v);
   }
 }
 
@@ -359,7 +390,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc_ops(const int4* __restrict__ key
         }
       }
       const int off = (r >> 3) * 256 + kc * 128 + (r & 7) * 16;
-      store_row64<BF16>(chunk + off, chunk + 32 * N + off, v);
+      store_row64<BF16>(chunk + off, 32 * N, limbs_of(BF16, G.l3, ks), v);
     }
   }
 }
@@ -378,13 +409,14 @@ __host__ __device__ constexpr int degree_of(int m) {
 // when e is not in its list.  Warp 0 lane 0 streams each source's A slices
 // once, plus the K slices of every target that uses it; warp 1 (target 0) and
 // warp 3 (target 1) issue the MMAs into their own 256-column halves of TMEM.
-template <int P, bool BF16, int NT>
+template <int P, bool BF16, int NT, int L3>
 __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
     k_m2l_tc(const int32_t* __restrict__ gtarget, const int64_t* __restrict__ goff,
              const int32_t* __restrict__ gsrc, const int32_t* __restrict__ gop, const int32_t* __restrict__ level,
              double side, int nc, int B, int nsb, const TcRing R, const unsigned char* __restrict__ QP,
              const unsigned char* __restrict__ ops, float* L, int* err) {
-  constexpr TcLayout G = tc_layout(P, BF16);
+  constexpr TcLayout G = tc_layout(P, BF16, L3);
+  constexpr bool A_UNIFORM = !BF16 || G.l3 == 0 || G.l3 >= G.KS;  // every k-step has lmax limbs
   static_assert(G.valid, "no tensor-core layout for this order");
   static_assert(NT == 1 || G.tmem_cols <= 256, "two targets need two 256-column accumulators");
   constexpr int TMEM_COLS = NT == 1 ? G.tmem_cols : 512;
@@ -392,7 +424,9 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
   uint64_t* full = (uint64_t*)(sm + (size_t)R.nslots * R.slot_bytes);
   uint64_t* empty = full + R.nslots;
   uint64_t* done = empty + R.nslots;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* gdone = done + 1;  // promotion: MMAs of a source group complete
+  uint64_t* gfree = done + 2;  // promotion: the promoted columns are read and zeroed
+  uint32_t* tmem_slot = (uint32_t*)(done + 3);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* counts = (int*)(tmem_slot + 2);  // slots issued, slots consumed by each issuer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -405,6 +439,8 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
       mbar_init(&empty[i], NT);  // one commit per issuer
     }
     mbar_init(done, NT);
+    mbar_init(gdone, 1);
+    mbar_init(gfree, 4);  // the four epilogue warps
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
     counts[0] = counts[1] = counts[2] = 0;
@@ -445,14 +481,22 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
             *abort_flag = 1;
             break;
           }
-          const int k0 = st * R.kps;
+          const int k0 = st * R.kps, nk = min(R.kps, G.KS - k0);
           const uint32_t fb = full0 + 8 * slot, dst = ring0 + slot * R.slot_bytes;
-          const uint32_t ab = (uint32_t)(min(R.kps, G.KS - k0) * G.a_bytes), kb = (uint32_t)R.step_kb[st];
+          const uint32_t kb = (uint32_t)R.step_kb[st];
+          uint32_t ab = 0;  // A bytes of the step: the used limbs of each k-step
+          for (int j = 0; j < nk; j++) ab += (uint32_t)(limbs_of(BF16, G.l3, k0 + j) * TC_SLICE);
           uint32_t bytes = ab;
 #pragma unroll
           for (int t = 0; t < NT; t++) bytes += O[t] >= 0 ? kb : 0u;
           expect_tx(fb, bytes);
-          bulk_load(dst, a + (int64_t)k0 * G.a_bytes, ab, fb);
+          if (A_UNIFORM) {
+            bulk_load(dst, a + (int64_t)k0 * G.a_bytes, ab, fb);
+          } else {
+            for (int j = 0; j < nk; j++)
+              bulk_load(dst + j * G.a_bytes, a + (int64_t)(k0 + j) * G.a_bytes,
+                        (uint32_t)(limbs_of(BF16, G.l3, k0 + j) * TC_SLICE), fb);
+          }
 #pragma unroll
           for (int t = 0; t < NT; t++)
             if (O[t] >= 0)
@@ -477,6 +521,7 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
     if (lane == 0) {
       int slot = 0, n = 0;
       uint32_t phase = 0, acc = 0;  // acc = 0 until the first source of this target has started D
+      uint32_t pphase = 0;          // promotion handshakes done
       bool bad = false;
       // one target per CTA: every source is in its list, no operator index is needed here
       int32_t O = NT == 1 ? 0 : gop[e0 * NT + t];
@@ -501,17 +546,24 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
               const uint32_t as = sa + j * G.a_bytes;
               const uint64_t ad = sdesc(as);
               const uint32_t kc = kb0 + G.ks_off[ks];  // k-step chunk: hi rows, then lo rows
+              const int nl = limbs_of(BF16, G.l3, ks);  // 1, 2 or 3 (compile-time after unrolling)
 #pragma unroll
               for (int r0 = 0; r0 < 512; r0 += 256) {
                 if (r0 < G.Nks[ks]) {
                   const int nrow = (G.Nks[ks] - r0 < 256) ? G.Nks[ks] - r0 : 256;  // MMA N <= 256
                   const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, nrow);
                   const uint32_t dcol = tmem + t * 256 + r0;
+                  const uint32_t kl = 32 * G.Nks[ks];  // K limbs are 32 N bytes apart
                   const uint64_t bd = sdesc(kc + 32 * r0);
                   mma<BF16>(dcol, ad, bd, id, ks == 0 ? acc : 1u);
-                  if constexpr (BF16) {
-                    mma<BF16>(dcol, ad, sdesc(kc + 32 * G.Nks[ks] + 32 * r0), id, 1u);  // hi x lo
-                    mma<BF16>(dcol, sdesc(as + TC_SLICE), bd, id, 1u);                  // lo x hi
+                  if (nl >= 2) {  // products of limb orders 1: hi x mid, mid x hi
+                    mma<BF16>(dcol, ad, sdesc(kc + kl + 32 * r0), id, 1u);
+                    mma<BF16>(dcol, sdesc(as + TC_SLICE), bd, id, 1u);
+                  }
+                  if (nl >= 3) {  // limb order 2: hi x lo, mid x mid, lo x hi
+                    mma<BF16>(dcol, ad, sdesc(kc + 2 * kl + 32 * r0), id, 1u);
+                    mma<BF16>(dcol, sdesc(as + TC_SLICE), sdesc(kc + kl + 32 * r0), id, 1u);
+                    mma<BF16>(dcol, sdesc(as + 2 * TC_SLICE), bd, id, 1u);
                   }
                 }
               }
@@ -529,6 +581,17 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
         }
         if (O >= 0) acc = 1u;
         O = On;
+        // promotion: hand the leading columns to the epilogue warps every prom_group sources
+        if (NT == 1 && R.prom_group > 0 && !bad && ((e - e0 + 1) % R.prom_group) == 0 && e + 1 < e1) {
+          mma_commit(smem_u32(gdone));
+          if (!mbar_wait(smem_u32(gfree), pphase, abort_flag)) {
+            if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+            *abort_flag = 1;
+            bad = true;
+          }
+          pphase ^= 1u;
+          tc_fence_after();
+        }
       }
       counts[1 + t] = n;
       mma_commit(smem_u32(done));  // arrives when every MMA issued above has completed
@@ -537,6 +600,35 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
   } else if (warp >= 4) {
     // ---- epilogue: warp 4 + q reads TMEM lanes 32q .. 32q + 31 (states)
     const int q = warp - 4;
+    // promotion: the leading columns are summed here in FP32 (round to nearest)
+    // and zeroed in TMEM every prom_group sources, so that the accumulator
+    // never carries a large running value of the cancelling low-degree terms
+    float tot[64];
+#pragma unroll
+    for (int i = 0; i < 64; i++) tot[i] = 0.f;
+    const int nprom = (NT == 1 && R.prom_group > 0) ? (int)((e1 - e0 - 1) / R.prom_group) : 0;
+    for (int g = 0; g < nprom; g++) {
+      if (!mbar_wait(smem_u32(gdone), (uint32_t)(g & 1), abort_flag)) {
+        if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        if (c < R.prom_chunks) {
+          uint32_t r[16];
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * c);
+          tmem_ld16(ta, r);
+#pragma unroll
+          for (int i = 0; i < 16; i++) tot[16 * c + i] += __uint_as_float(r[i]);
+          tmem_zero16(ta);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(gfree));
+    }
     const bool ok = mbar_wait(smem_u32(done), 0, nullptr);
     if (!ok) {
       atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
@@ -560,7 +652,9 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
 #pragma unroll
             for (int i = 0; i < 16; i++) {
               const int m = c0 + i;
-              if (m < G.nc) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * __uint_as_float(r[i]);
+              float v = __uint_as_float(r[i]);
+              if (c0 < 64 && t == 0) v += tot[(c0 < 64 ? c0 : 0) + i];  // promoted part (zero when not promoting)
+              if (m < G.nc) Lt[(int64_t)m * B] = ((degree_of(m) & 1) ? -inv : inv) * v;
             }
           }
         }
@@ -596,35 +690,45 @@ struct KeyHash {
   }
 };
 
-TcLayout layout_of(const Plan& P) { return tc_layout(P.p, P.opt.precision == DEMAG_MIXED_BF16X3); }
+bool split_bf16(const Plan& P) {
+  return P.opt.precision == DEMAG_MIXED_BF16X3 || P.opt.precision == DEMAG_MIXED_BF16X6;
+}
+TcLayout layout_of(const Plan& P) { return tc_layout(P.p, split_bf16(P), P.tc_l3); }
 
-template <int PP, bool BF16, int NT>
+template <int PP, bool BF16, int NT, int L3>
 void launch_fixed(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
   static size_t attr = 0;
   const size_t smem = ring_smem(R);
   if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT, L3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
   const int nsb = (B + TC_M - 1) / TC_M;
   if (NT == 1) {
     dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)nsb);
-    k_m2l_tc<PP, BF16, NT><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.tc_g1_off, P.m2l_src, P.m2l_op,
-                                                          P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+    k_m2l_tc<PP, BF16, NT, L3><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.tc_g1_off, P.m2l_src, P.m2l_op,
+                                                              P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L,
+                                                              err);
   } else {
     dim3 grid((unsigned)P.tc_n_g2, (unsigned)nsb);
-    k_m2l_tc<PP, BF16, NT><<<grid, TC_THREADS, smem, s>>>(P.tc_g2_tgt, P.tc_g2_off, P.tc_g2_src, P.tc_g2_op,
-                                                          P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L, err);
+    k_m2l_tc<PP, BF16, NT, L3><<<grid, TC_THREADS, smem, s>>>(P.tc_g2_tgt, P.tc_g2_off, P.tc_g2_src, P.tc_g2_op,
+                                                              P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L,
+                                                              err);
   }
   DM_LAUNCH("k_m2l_tc");
 }
 
+// compiled variants: TF32 and two-limb split BF16 with one or two targets per
+// CTA; three-limb split BF16 with one target per CTA
 template <int PP, bool BF16>
 void launch_nt(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
-  if constexpr (tc_layout(PP, BF16).tmem_cols <= 256) {
-    if (R.nt == 2) return launch_fixed<PP, BF16, 2>(P, R, B, QP, L, err, s);
+  if constexpr (BF16) {
+    if (P.tc_l3 == TC_L3_ALL) return launch_fixed<PP, BF16, 1, TC_L3_ALL>(P, R, B, QP, L, err, s);
   }
-  launch_fixed<PP, BF16, 1>(P, R, B, QP, L, err, s);
+  if constexpr (tc_layout(PP, BF16, 0).tmem_cols <= 256) {
+    if (R.nt == 2) return launch_fixed<PP, BF16, 2, 0>(P, R, B, QP, L, err, s);
+  }
+  launch_fixed<PP, BF16, 1, 0>(P, R, B, QP, L, err, s);
 }
 
 template <bool BF16>
@@ -639,7 +743,7 @@ void launch_order(Plan& P, const TcRing& R, int B, const unsigned char* QP, floa
 }
 
 void launch_main(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
-  if (P.opt.precision == DEMAG_MIXED_BF16X3)
+  if (split_bf16(P))
     launch_order<true>(P, R, B, QP, L, err, s);
   else
     launch_order<false>(P, R, B, QP, L, err, s);
@@ -705,8 +809,10 @@ void tune_ring(Plan& P, const TcLayout& G) {
 }
 
 bool current_ring(const Plan& P, const TcLayout& G, TcRing& R) {
-  if (P.tc_kps > 0 && make_ring(G, P.tc_nt, P.tc_kps, P.tc_budget, R)) return true;
-  default_ring(G, P.opt.m2l_targets_per_cta, P.opt.m2l_kps, R);
+  if (!(P.tc_kps > 0 && make_ring(G, P.tc_nt, P.tc_kps, P.tc_budget, R)))
+    default_ring(G, P.opt.m2l_targets_per_cta, P.opt.m2l_kps, R);
+  R.prom_group = R.nt == 1 ? P.tc_prom_group : 0;
+  R.prom_chunks = std::min(4, std::max(1, (P.tc_prom_rows + 15) / 16));
   return R.nslots >= 2;
 }
 
@@ -721,15 +827,16 @@ void build_ops(Plan& P, const TcLayout& G, const std::vector<int4>& keys) {
   DM_CUDA(cudaStreamSynchronize(s));
 }
 
-bool tc_enabled(const Plan& P) {
-  return (P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3) && P.tc_ops != nullptr;
-}
+bool tc_enabled(const Plan& P) { return (P.opt.precision == DEMAG_MIXED_TF32 || split_bf16(P)) && P.tc_ops != nullptr; }
 
 }  // namespace
 
 void build_m2l_tc(Plan& P) {
-  if (P.opt.precision != DEMAG_MIXED_TF32 && P.opt.precision != DEMAG_MIXED_BF16X3) return;
+  if (P.opt.precision != DEMAG_MIXED_TF32 && !split_bf16(P)) return;
   if (P.n_m2l == 0 || !tc_order(P.p)) return;  // the CUDA-core M2L runs instead
+  P.tc_prom_group = P.opt.m2l_promote < 0 ? 0 : (P.opt.m2l_promote == 0 ? 8 : P.opt.m2l_promote);
+  P.tc_prom_rows = P.opt.m2l_promote_rows > 0 ? P.opt.m2l_promote_rows : 16;
+  P.tc_l3 = P.opt.precision == DEMAG_MIXED_BF16X6 ? TC_L3_ALL : 0;
   const TcLayout G = layout_of(P);
   if (!G.valid) return;
   cudaStream_t s = P.stream;
@@ -835,10 +942,11 @@ bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, 
   TcRing R;
   if (!current_ring(P, G, R)) return false;
   const int nsb = (B + TC_M - 1) / TC_M;
+  const dim3 grid((unsigned)P.ncells, (unsigned)nsb);
   if (G.bf16)
-    k_m2l_tc_pack<true><<<dim3((unsigned)P.ncells, (unsigned)nsb), TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, QP);
+    k_m2l_tc_pack<true><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, G.l3, QP);
   else
-    k_m2l_tc_pack<false><<<dim3((unsigned)P.ncells, (unsigned)nsb), TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, QP);
+    k_m2l_tc_pack<false><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, G.l3, QP);
   DM_LAUNCH("k_m2l_tc_pack");
   launch_main(P, R, B, QP, L, err, s);
   return true;

@@ -1,0 +1,68 @@
+"""Full-size configurations other than the benchmark's (parity cases, not
+bench lines):
+
+* the thin film 2000 x 1000 x 10 (1,990,656 tets, 500,259 nodes) with a Landau
+  flux-closure magnetisation plus 5 % random tilt, p = 8, theta = 0.5: the FP64
+  GPU FMM against the oracle FMM on sampled target leaves computed one by one,
+  and the split-BF16 tensor-core path against FP64 per state;
+* the benchmark ball (223,668 tets) with a uniform magnetisation -- smooth M
+  makes the far field a sum of large cancelling dipole terms, the hardest case
+  for the tensor-core M2L's accumulation.
+
+Both check the effect of promoting the leading M2L accumulator rows to FP32
+registers (the default): without it the film misses the 1e-4 bar."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1606_00247_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def test_film_full_size(orc):
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.thin_film()
+    assert tets.shape[0] == 1990656 and nodes.shape[0] == 500259
+    M = np.stack([inputs.landau_m(nodes), inputs.landau_m(nodes, seed=inputs.MAG_SEED + 7)])
+    Md = torch.as_tensor(M, device="cuda")
+    p64 = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="fp64", near_mode=1, max_batch=2)
+    u64, H64 = p64.eval(Md)
+    ex = p64.export_tree()
+    del p64
+    # FP64 GPU vs the oracle FMM on 12 sampled target leaves (state 0)
+    tr = orc.Tree(nodes, tets, 128, 0.5)
+    leaves = np.where((ex["cell_child"][:, 1] == 0) & (ex["cell_ranges"][:, 3] > ex["cell_ranges"][:, 2]))[0]
+    pick = leaves[np.linspace(0, len(leaves) - 1, 12).astype(int)]
+    ref = tr.fmm(M[0], 8, target_leaves=pick)
+    sel = np.concatenate([ex["node_perm"][ex["cell_ranges"][c, 2]:ex["cell_ranges"][c, 3]] for c in pick])
+    g = u64[0].cpu().numpy()[sel]
+    assert np.linalg.norm(g - ref[sel]) / np.linalg.norm(ref[sel]) < 1e-10
+    # split BF16 (promotion on by default) vs FP64, per state; and without promotion
+    errs = {}
+    for promote in (0, -1):
+        pl = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1, max_batch=2,
+                  m2l_promote=promote)
+        u, H = pl.eval(Md)
+        errs[promote] = max(max(rel(u[k], u64[k]), rel(H[k], H64[k])) for k in range(2))
+        del pl
+    assert errs[0] <= 1e-4, errs
+    assert errs[0] < errs[-1] / 3, errs  # promotion is what brings the film under the bar
+
+
+def test_ball_uniform_m_tensor_core():
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=inputs.SPHERE_200K_H)
+    M = torch.as_tensor(np.stack([inputs.uniform_m(nodes.shape[0], d) for d in ((0, 0, 1), (1, 0, 0))]),
+                        device="cuda")
+    u64, H64 = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, near_mode=1, max_batch=2).eval(M)
+    for prec, bar in (("bf16x3", 1e-5), ("bf16x6", 1e-5)):
+        u, H = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision=prec, near_mode=1, max_batch=2).eval(M)
+        for k in range(2):
+            assert rel(u[k], u64[k]) <= bar and rel(H[k], H64[k]) <= bar, (prec, k)

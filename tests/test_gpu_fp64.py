@@ -109,3 +109,20 @@ def test_sampled_targets_on_larger_sphere(orc):
     sel = np.concatenate([ex["node_perm"][ex["cell_ranges"][c, 2]:ex["cell_ranges"][c, 3]] for c in leaves])
     u, _ = _plan(nodes, tets, p=6, leaf_size=32).eval(M)
     assert rel_l2(u.cpu().numpy()[sel], ref[sel]) < 1e-10
+
+
+def test_fmm_error_vs_direct_decays_with_p():
+    """The FP64 GPU FMM against the direct sum of the same library (theta -> 0,
+    every pair analytic): the truncation error falls with p (Sec. 2.2 error
+    model) and is small at p = 8."""
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=0.2)
+    M = inputs.gaussian_unit_m(nodes.shape[0])
+    ud, _ = Plan(nodes, tets, p=2, leaf_size=8, theta=1e-6, near_mode=0).eval(M)
+    errs = []
+    for p in (2, 4, 6, 8):
+        u, _ = Plan(nodes, tets, p=p, leaf_size=8, theta=0.5, near_mode=1).eval(M)
+        errs.append(float(torch.linalg.norm(u - ud) / torch.linalg.norm(ud)))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4, errs

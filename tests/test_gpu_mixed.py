@@ -80,8 +80,8 @@ def test_tensor_core_m2l_vs_fp64(prec, p, B):
     eh = per_state(Htc.cpu().numpy(), H64.cpu().numpy())
     bar = 1e-4 if prec == "bf16x3" else 1e-3
     assert eu <= bar and eh <= bar, (eu, eh)
-    if prec == "bf16x3":
-        assert eu < 5e-5 and eh < 5e-5, (eu, eh)
+    if prec == "bf16x3":  # with the accumulator rows promoted (default) the split-BF16 M2L is ~1e-6
+        assert eu < 1e-5 and eh < 1e-5, (eu, eh)
 
 
 @pytest.mark.parametrize("scale", [1e-3, 1e3])
@@ -157,9 +157,10 @@ def test_tensor_core_ring_shape_does_not_change_results():
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_tensor_core_two_target_groups_match_one_target(prec):
     """Two targets per CTA over the union of their source lists (each source's
-    moments loaded once) must give bit-identical L to one target per CTA: the
-    MMA sequence of every target is the same, sources absent from a target's
-    list only skip its MMAs."""
+    moments loaded once) against one target per CTA.  One-target CTAs take each
+    target's sources by distance, two-target CTAs in index order, so the two
+    agree to the accumulation rounding of the tensor core, and both meet the
+    bar against FP64."""
     from paper_1606_00247_gb300 import _lib as L
 
     nodes, tets = inputs.sphere(h=0.13)
@@ -171,6 +172,8 @@ def test_tensor_core_two_target_groups_match_one_target(prec):
               m2l_kps=3)
     assert b.stats()["m2l_targets_per_cta"] == 1 and b.stats()["m2l_kps"] == 3
     ub, Hb = b.eval(M)
-    assert torch.equal(ua, ub) and torch.equal(Ha, Hb)
     u64, _ = _plan(nodes, tets, p=8, leaf_size=32, max_batch=128, near_mode=1).eval(M)
-    assert per_state(ua.cpu().numpy(), u64.cpu().numpy()) <= (1e-4 if prec == "bf16x3" else 1e-3)
+    bar = 1e-4 if prec == "bf16x3" else 1e-3
+    assert per_state(ua.cpu().numpy(), u64.cpu().numpy()) <= bar
+    assert per_state(ub.cpu().numpy(), u64.cpu().numpy()) <= bar
+    assert per_state(ua.cpu().numpy(), ub.cpu().numpy()) <= bar
