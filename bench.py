@@ -190,6 +190,7 @@ def alu_peak_tflops(kind, sm_mhz):
 # configuration and kernel version; any other configuration reports null
 NCU_TRAFFIC = {
     # (stage, precision, p, leaf, batch, n_tets, targets per CTA, kps): bytes
+    ("m2l", "bf16x3", 8, 128, 128, 223668, 1, 2): 25.674e9 + 0.244e9,
 }
 
 
