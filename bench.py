@@ -194,7 +194,14 @@ NCU_TRAFFIC = {
 }
 
 
-def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
+def m2l_on_tensor_cores(precision, B, table_batch):
+    """The tensor-core precisions run the FP32 table M2L on CUDA cores up to
+    m2l_table_batch states (0: the library default of 16; < 0: never)."""
+    limit = 16 if table_batch == 0 else max(table_batch, 0)
+    return precision in ("tf32", "bf16x3", "bf16x6") and B > limit
+
+
+def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz, tensor_m2l=True):
     """Roofline of the dominant stage from its live per-stage CUDA-event time."""
     ms = stats["stage_ms"]
     dom = max(ms, key=lambda k: ms[k])
@@ -216,7 +223,7 @@ def roofline_for(stats, steps_profiled, precision, peaks, sm_mhz):
     elif dom == "p2p":
         work = 2.0 * 3 * stats["n_near_cols"] * B / launches_per_eval
         note = f"near-field application, 2 flops per stored coefficient per state, {kind}"
-    if work is not None and dom == "m2l" and precision in ("tf32", "bf16x3"):
+    if work is not None and dom == "m2l" and precision in ("tf32", "bf16x3") and tensor_m2l:
         # tcgen05 M2L timed inside a long step: the sustained measured BF16 rate is
         # the denominator (TF32: x the nominal TF32/BF16 ratio 1.1 / 2.25 PFLOP/s)
         achieved = work / per_launch_s / 1e12
@@ -303,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
     nodes, tets = make_mesh(w)
     B = args.batch
     plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
-                near_mode=args.near_mode, max_batch=B, device=dev, autotune=bool(args.autotune))
+                near_mode=args.near_mode, max_batch=B, device=dev, autotune=bool(args.autotune),
+                m2l_table_batch=args.m2l_table_batch)
     st0 = plan.stats()
     M = torch.as_tensor(make_M(nodes.shape[0], B, seed_offset=rank), device=dev)
     u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device=dev)
@@ -345,7 +353,8 @@ def run_ours(args, rank, world, local_rank):
 
     # live per-stage timing pass (CUDA events on the eval stream, inside the library)
     prof = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
-                near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=bool(args.autotune))
+                near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=bool(args.autotune),
+                m2l_table_batch=args.m2l_table_batch)
     for _ in range(2):
         prof.eval(M, u, H)
     prof.reset_timers()
@@ -356,7 +365,8 @@ def run_ours(args, rank, world, local_rank):
     pst = prof.stats()
     pst["_batch"] = B
     pst["near_mode"] = args.near_mode
-    roof = roofline_for(pst, nprof, args.precision, measured_peaks(), clk.get("sm_mhz"))
+    roof = roofline_for(pst, nprof, args.precision, measured_peaks(), clk.get("sm_mhz"),
+                        m2l_on_tensor_cores(args.precision, B, args.m2l_table_batch))
     prof.close()
 
     # FP64 GPU FMM of the same plan settings: throughput, and the accuracy gate
@@ -506,6 +516,8 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--autotune", type=int, default=1, help="1: time the M2L launch shapes at plan time")
+    ap.add_argument("--m2l-table-batch", type=int, default=0,
+                    help="largest batch run by the FP32 table M2L in the tensor-core precisions (0: default, -1: never)")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--theta", type=float, default=0.0)

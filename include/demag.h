@@ -92,10 +92,18 @@ typedef struct {
                           so without this the error follows the running
                           value, which for smooth M is far above the result */
   int m2l_promote_rows; /* rows moved (rounded up to 16, at most 64); 0 = 16 */
+  int m2l_table_batch; /* TF32 / split BF16: batches B <= this run the M2L in
+                          FP32 on CUDA cores, from a per-plan table of the
+                          translation derivatives (p in {4, 6, 8}); larger
+                          batches use the tensor cores, whose tiles hold 128
+                          states.  0 = default (16), < 0 = never.  The FP32
+                          precision always uses the table M2L when there is
+                          one.                                              */
 } demag_options;
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
- * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0. */
+ * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0,
+ * m2l_table_batch=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and

@@ -106,6 +106,7 @@ void demag_options_default(demag_options* o) {
   o->m2l_kps = 0;
   o->m2l_promote = 0;
   o->m2l_promote_rows = 0;
+  o->m2l_table_batch = 0;
   o->profile = 0;
 }
 

@@ -169,6 +169,8 @@ struct Plan {
   int64_t n_tc_ops = 0;
   unsigned char* tc_ops = nullptr;
   int32_t* m2l_op = nullptr;        // n_m2l
+  float* m2l_tab = nullptr;         // n_tc_ops x nc: FP32 b_k(v) per key (CUDA-core M2L)
+  int32_t* m2l_tab_opdl = nullptr;  // n_m2l: key index | (level difference & 255) << 24
   int tc_nt = 1, tc_kps = 0, tc_budget = 0;  // M2L launch shape: targets per CTA, k-steps per slot, ring bytes
   int tc_l3 = 0;                    // split BF16: k-steps in three limbs (0 = none, 99 = all)
   int tc_prom_group = 0, tc_prom_rows = 16;  // accumulator promotion: sources per group (0 = off), rows
@@ -277,10 +279,25 @@ void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H
 void build_near_field(Plan& P);
 void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s);
 void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s);
+struct M2lKeys {  // distinct translation keys (dl, lattice offset) and the key of every M2L pair
+  bool ok = false;
+  std::vector<int4> keys;
+  std::vector<int64_t> off;           // host copy of m2l_off
+  std::vector<int32_t> src, op;       // host copies of m2l_src and of the key index per pair
+};
 // mixed-precision far field (fmm32.cu)
 void build_mixed_operators(Plan& P);
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaStream_t s);  // m2l32.cu
+// FP32 table-driven M2L on CUDA cores (m2l32.cu): derivative table per key at
+// plan time; launch returns false when the plan has no table
+void build_m2l_tab(Plan& P, const M2lKeys& K);
+bool launch_m2l32_tab(Plan& P, int B, const float* Q, float* L, cudaStream_t s);
+// largest batch for which the tensor-core precisions run the table-driven FP32
+// M2L instead of the tensor-core one (whose tiles hold 128 states)
+inline int m2l_table_batch(const Plan& P) {
+  return P.opt.m2l_table_batch < 0 ? 0 : (P.opt.m2l_table_batch == 0 ? 16 : P.opt.m2l_table_batch);
+}
 // several plans in one submission (multi.cu); cached graphs of a plan are
 // dropped before the plan or its workspace goes away
 void eval_multi(Plan* const* plans, int n, const double* const* M, const int* batch, double* const* u,
@@ -289,7 +306,8 @@ void multi_forget_plan(const Plan* P);
 // tensor-core M2L (m2l_tc.cu): operator table at plan time; bytes of the packed
 // moments for B states (0 when the tensor-core M2L is off); packs Q into QP and
 // runs the M2L (false: not available for this plan, use the CUDA-core M2L)
-void build_m2l_tc(Plan& P);
+M2lKeys build_m2l_keys(Plan& P);      // also fills P.m2l_op
+void build_m2l_tc(Plan& P, const M2lKeys& K);
 size_t m2l_tc_pack_bytes(const Plan& P, int B);
 bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, int* err, cudaStream_t s);
 

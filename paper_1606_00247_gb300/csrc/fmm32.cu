@@ -502,7 +502,11 @@ void build_mixed_operators(Plan& P) {
                                                              P.nc1, P.Ghat32);
     DM_LAUNCH("k_ghat32");
   }
-  build_m2l_tc(P);
+  if (P.n_m2l > 0) {
+    const M2lKeys K = build_m2l_keys(P);
+    build_m2l_tc(P, K);
+    build_m2l_tab(P, K);
+  }
 }
 
 void eval_mixed(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s) {
@@ -544,11 +548,13 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   clk.end();
   clk.begin(DEMAG_STAGE_M2L);
   DM_CUDA(cudaMemsetAsync(W.L32, 0, sizeof(float) * P.ncells * nc * B, s));
+  const bool tc_prec = P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3 ||
+                       P.opt.precision == DEMAG_MIXED_BF16X6;
   if (P.h_m2l_targets.empty()) {
-  } else if ((P.opt.precision == DEMAG_MIXED_TF32 || P.opt.precision == DEMAG_MIXED_BF16X3 ||
-              P.opt.precision == DEMAG_MIXED_BF16X6) &&
-             launch_m2l_tc(P, B, W.Q32, W.QP, W.L32, W.err, s)) {
+  } else if (tc_prec && B > m2l_table_batch(P) && launch_m2l_tc(P, B, W.Q32, W.QP, W.L32, W.err, s)) {
     clk.launched(2);
+  } else if ((!tc_prec || B <= m2l_table_batch(P)) && launch_m2l32_tab(P, B, W.Q32, W.L32, s)) {
+    clk.launched();
   } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s)) {
     clk.launched();
   } else {

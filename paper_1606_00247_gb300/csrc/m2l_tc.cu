@@ -831,32 +831,27 @@ bool tc_enabled(const Plan& P) { return (P.opt.precision == DEMAG_MIXED_TF32 || 
 
 }  // namespace
 
-void build_m2l_tc(Plan& P) {
-  if (P.opt.precision != DEMAG_MIXED_TF32 && !split_bf16(P)) return;
-  if (P.n_m2l == 0 || !tc_order(P.p)) return;  // the CUDA-core M2L runs instead
-  P.tc_prom_group = P.opt.m2l_promote < 0 ? 0 : (P.opt.m2l_promote == 0 ? 8 : P.opt.m2l_promote);
-  P.tc_prom_rows = P.opt.m2l_promote_rows > 0 ? P.opt.m2l_promote_rows : 16;
-  P.tc_l3 = P.opt.precision == DEMAG_MIXED_BF16X6 ? TC_L3_ALL : 0;
-  const TcLayout G = layout_of(P);
-  if (!G.valid) return;
+M2lKeys build_m2l_keys(Plan& P) {
+  M2lKeys K;
+  if (P.n_m2l == 0) return K;
   cudaStream_t s = P.stream;
   const int64_t nc = P.ncells;
   std::vector<uint64_t> prefix(nc);
-  std::vector<int32_t> lev(nc), src(P.n_m2l);
-  std::vector<int64_t> off(nc + 1);
+  std::vector<int32_t> lev(nc);
+  K.off.resize(nc + 1);
+  K.src.resize(P.n_m2l);
   DM_CUDA(cudaMemcpyAsync(prefix.data(), P.cell_prefix, nc * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   DM_CUDA(cudaMemcpyAsync(lev.data(), P.cell_level, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  DM_CUDA(cudaMemcpyAsync(off.data(), P.m2l_off, (nc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  DM_CUDA(cudaMemcpyAsync(src.data(), P.m2l_src, P.n_m2l * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(K.off.data(), P.m2l_off, (nc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DM_CUDA(cudaMemcpyAsync(K.src.data(), P.m2l_src, P.n_m2l * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DM_CUDA(cudaStreamSynchronize(s));
   std::vector<std::array<int64_t, 3>> kc(nc);
   for (int64_t c = 0; c < nc; c++) cell_coords(prefix[c], lev[c], kc[c].data());
   std::unordered_map<std::array<int64_t, 4>, int32_t, KeyHash> index;
-  std::vector<int4> keys;
-  std::vector<int32_t> op(P.n_m2l);
+  K.op.resize(P.n_m2l);
   for (int64_t T = 0; T < nc; T++)
-    for (int64_t e = off[T]; e < off[T + 1]; e++) {
-      const int32_t S = src[e];
+    for (int64_t e = K.off[T]; e < K.off[T + 1]; e++) {
+      const int32_t S = K.src[e];
       const int dl = lev[T] - lev[S];
       std::array<int64_t, 4> key{dl, 0, 0, 0};
       for (int a = 0; a < 3; a++)
@@ -865,19 +860,36 @@ void build_m2l_tc(Plan& P) {
       auto f = index.find(key);
       if (f == index.end()) {
         for (int a = 1; a < 4; a++)
-          if (key[a] > INT32_MAX || key[a] < INT32_MIN) return;  // beyond the table's key range
-        f = index.emplace(key, (int32_t)keys.size()).first;
-        keys.push_back(make_int4(dl, (int)key[1], (int)key[2], (int)key[3]));
+          if (key[a] > INT32_MAX || key[a] < INT32_MIN) return M2lKeys{};  // beyond the table's key range
+        f = index.emplace(key, (int32_t)K.keys.size()).first;
+        K.keys.push_back(make_int4(dl, (int)key[1], (int)key[2], (int)key[3]));
       }
-      op[e] = f->second;
+      K.op[e] = f->second;
     }
   P.m2l_op = dalloc<int32_t>(P, P.n_m2l);
-  DM_CUDA(cudaMemcpyAsync(P.m2l_op, op.data(), P.n_m2l * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  P.n_tc_ops = (int64_t)keys.size();
+  DM_CUDA(cudaMemcpyAsync(P.m2l_op, K.op.data(), P.n_m2l * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  DM_CUDA(cudaStreamSynchronize(s));
+  P.n_tc_ops = (int64_t)K.keys.size();
+  K.ok = true;
+  return K;
+}
+
+void build_m2l_tc(Plan& P, const M2lKeys& K) {
+  if (P.opt.precision != DEMAG_MIXED_TF32 && !split_bf16(P)) return;
+  if (!K.ok || !tc_order(P.p)) return;  // the CUDA-core M2L runs instead
+  P.tc_prom_group = P.opt.m2l_promote < 0 ? 0 : (P.opt.m2l_promote == 0 ? 8 : P.opt.m2l_promote);
+  P.tc_prom_rows = P.opt.m2l_promote_rows > 0 ? P.opt.m2l_promote_rows : 16;
+  P.tc_l3 = P.opt.precision == DEMAG_MIXED_BF16X6 ? TC_L3_ALL : 0;
+  const TcLayout G = layout_of(P);
+  if (!G.valid) return;
+  cudaStream_t s = P.stream;
+  const std::vector<int64_t>& off = K.off;
+  const std::vector<int32_t>& src = K.src;
+  const std::vector<int32_t>& op = K.op;
   if (G.bf16)
-    build_ops<true>(P, G, keys);
+    build_ops<true>(P, G, K.keys);
   else
-    build_ops<false>(P, G, keys);
+    build_ops<false>(P, G, K.keys);
   // groups of one target: the target's own list
   const int64_t nT = (int64_t)P.h_m2l_targets.size();
   std::vector<int64_t> g1(nT + 1);

@@ -109,6 +109,28 @@ SPHERE_200K_H = 0.0505
 SPHERE_500K_H = 0.0372
 
 
+def batch_meshes(n=64, min_tets=1e4, max_tets=3e5, seed=MESH_SEED + 4):
+    """Meshes of uneven size for many-mesh submissions: target sizes
+    log-uniform in [min_tets, max_tets], types round-robin Kuhn cube, ball,
+    ellipsoid with axis ratios (1, a, b), a, b ~ U[1, 4].  Ball and ellipsoid
+    spacings are scaled from the ball of 223,668 tets at SPHERE_200K_H."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(min_tets), np.log(max_tets), n))
+    out = []
+    for i, size in enumerate(sizes):
+        kind = i % 3
+        if kind == 0:
+            k = max(2, int(round((size / 6.0) ** (1.0 / 3.0))))
+            out.append(kuhn_box((k, k, k)))
+        elif kind == 1:
+            out.append(sphere(h=SPHERE_200K_H * (223668.0 / size) ** (1.0 / 3.0), seed=seed + i))
+        else:
+            a, b = rng.uniform(1.0, 4.0, 2)
+            h = SPHERE_200K_H * (223668.0 * a * b / size) ** (1.0 / 3.0)
+            out.append(sphere(h=h, seed=seed + i, scale=(1.0, a, b)))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # magnetisations (nodal, shape (N_n, 3) or (B, N_n, 3))
 # ---------------------------------------------------------------------------

@@ -45,14 +45,19 @@ def test_film_full_size(orc):
     assert np.linalg.norm(g - ref[sel]) / np.linalg.norm(ref[sel]) < 1e-10
     # split BF16 (promotion on by default) vs FP64, per state; and without promotion
     errs = {}
-    for promote in (0, -1):
+    for promote in (0, -1):  # tensor-core M2L forced at this batch of 2
         pl = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1, max_batch=2,
-                  m2l_promote=promote)
+                  m2l_promote=promote, m2l_table_batch=-1)
         u, H = pl.eval(Md)
         errs[promote] = max(max(rel(u[k], u64[k]), rel(H[k], H64[k])) for k in range(2))
         del pl
     assert errs[0] <= 1e-4, errs
     assert errs[0] < errs[-1] / 3, errs  # promotion is what brings the film under the bar
+    # default at a batch of 2: the table-driven FP32 M2L on CUDA cores
+    pl = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1, max_batch=2)
+    u, H = pl.eval(Md)
+    err = max(max(rel(u[k], u64[k]), rel(H[k], H64[k])) for k in range(2))
+    assert err <= 1e-4, err
 
 
 def test_ball_uniform_m_tensor_core():
@@ -62,7 +67,8 @@ def test_ball_uniform_m_tensor_core():
     M = torch.as_tensor(np.stack([inputs.uniform_m(nodes.shape[0], d) for d in ((0, 0, 1), (1, 0, 0))]),
                         device="cuda")
     u64, H64 = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, near_mode=1, max_batch=2).eval(M)
-    for prec, bar in (("bf16x3", 1e-5), ("bf16x6", 1e-5)):
-        u, H = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision=prec, near_mode=1, max_batch=2).eval(M)
+    for prec, bar, tb in (("bf16x3", 1e-5, -1), ("bf16x6", 1e-5, -1), ("fp32", 1e-5, 0)):
+        u, H = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision=prec, near_mode=1, max_batch=2,
+                    m2l_table_batch=tb).eval(M)
         for k in range(2):
             assert rel(u[k], u64[k]) <= bar and rel(H[k], H64[k]) <= bar, (prec, k)

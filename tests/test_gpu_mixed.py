@@ -73,7 +73,7 @@ def test_tensor_core_m2l_vs_fp64(prec, p, B):
     nodes, tets = inputs.sphere(h=0.13)
     M = inputs.gaussian_unit_m(nodes.shape[0], batch=B)
     u64, H64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1).eval(M)
-    ptc = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision=prec)
+    ptc = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision=prec, m2l_table_batch=-1)
     assert ptc.stats()["n_m2l_ops"] > 0  # the tensor-core M2L ran (orders 4, 6, 8, 10)
     utc, Htc = ptc.eval(M)
     eu = per_state(utc.cpu().numpy(), u64.cpu().numpy())
@@ -82,6 +82,41 @@ def test_tensor_core_m2l_vs_fp64(prec, p, B):
     assert eu <= bar and eh <= bar, (eu, eh)
     if prec == "bf16x3":  # with the accumulator rows promoted (default) the split-BF16 M2L is ~1e-6
         assert eu < 1e-5 and eh < 1e-5, (eu, eh)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+@pytest.mark.parametrize("B", [1, 3, 32, 40])
+def test_table_m2l_vs_fp64(p, B):
+    """Table-driven FP32 M2L on CUDA cores (the FP32 precision at every batch,
+    the tensor-core precisions at small ones): one state per lane for B = 1
+    (32 sources per warp step), a ragged state slice for B = 3, a full 32-state
+    slice, and two slices with a ragged second one (B = 40).  The ball's octree
+    has leaves on several levels, so pairs with f_S != 1 are included."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=B, seed=70 + B)
+    p64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1)
+    ex = p64.export_tree()
+    lev = ex["cell_level"]
+    tgt = np.repeat(np.arange(len(lev)), np.diff(ex["m2l_off"]))
+    assert np.any(lev[tgt] != lev[ex["m2l_src"]])  # cross-level M2L pairs exist
+    u64, H64 = p64.eval(M)
+    u32, H32 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1, precision="fp32").eval(M)
+    eu = per_state(u32.cpu().numpy(), u64.cpu().numpy())
+    eh = per_state(H32.cpu().numpy(), H64.cpu().numpy())
+    assert eu < 2e-6 and eh < 2e-5, (eu, eh)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_small_batch_tensor_precisions_use_the_table_m2l(prec):
+    """At batches up to m2l_table_batch (default 16) the tensor-core precisions
+    run the same FP32 kernels as the FP32 precision: identical bits."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=4, seed=91)
+    a = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision="fp32").eval(M)
+    b = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec).eval(M)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    c = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec, m2l_table_batch=-1).eval(M)
+    assert not torch.equal(a[0], c[0])  # forced onto the tensor cores
 
 
 @pytest.mark.parametrize("scale", [1e-3, 1e3])
