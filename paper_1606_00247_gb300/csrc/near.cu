@@ -545,9 +545,119 @@ void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStre
   DM_LAUNCH("k_near_apply<double>");
 }
 
+// Small batches: one block of 256 threads per (target leaf, slice of BS <= 8
+// states), W streamed straight from HBM with one coalesced float4 load per
+// (column, target node) element and no staging -- the W of a leaf is contiguous
+// ([col][node]), so thread t = g NP + i (node i of a pass of NP nodes, column
+// group g of G = 256 / NP) reads consecutive elements for consecutive t and
+// the block sweeps the leaf's W front to back.  The NP threads of a column
+// share its M (L1 broadcast).  Per-thread partial sums are added over the
+// column groups in a fixed order, so the result does not depend on timing.
+// The tiles of the batched kernels hold 32 or 128 states, so for small B this
+// one reads W once per BS states instead of paying for the whole tile.
+constexpr int NS_THREADS = 256;
+constexpr int NEAR_SMALL_BATCH = 64;  // batches below this use k_near_apply32_s
+
+template <int BS>
+__device__ __forceinline__ void load_m(const float* __restrict__ mp, int B, int nlive, bool vec, float (&m)[3][BS]) {
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      if constexpr (BS % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < BS / 4; v++) {
+          const float4 x = *(const float4*)(mp + k * B + 4 * v);
+          m[k][4 * v] = x.x;
+          m[k][4 * v + 1] = x.y;
+          m[k][4 * v + 2] = x.z;
+          m[k][4 * v + 3] = x.w;
+        }
+      } else if constexpr (BS == 2) {
+        const float2 x = *(const float2*)(mp + k * B);
+        m[k][0] = x.x;
+        m[k][1] = x.y;
+      } else {
+        m[k][0] = mp[k * B];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+      for (int v = 0; v < BS; v++) m[k][v] = v < nlive ? mp[k * B + v] : 0.f;
+  }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(NS_THREADS) k_near_apply32_s(
+    const int32_t* __restrict__ targets, const int4* __restrict__ range, const int64_t* __restrict__ coloff,
+    const int32_t* __restrict__ cols, const int64_t* __restrict__ woff32, const float* __restrict__ W32,
+    const float* __restrict__ Ms, int B, float* u_s) {
+  __shared__ float red[NS_THREADS * BS];
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti];
+  const int ncol = (int)(coloff[ti + 1] - c0);
+  const float4* Wt = (const float4*)(W32 + woff32[ti]);
+  const int b0 = blockIdx.y * BS;
+  const int nlive = min(BS, B - b0);
+  const bool vec = nlive == BS && (B % BS) == 0;  // M rows of this slice are BS-aligned vectors
+  const int t = threadIdx.x;
+  for (int i0 = 0; i0 < nT; i0 += NS_THREADS) {
+    const int NP = min(NS_THREADS, nT - i0), G = NS_THREADS / NP;
+    const int i = t % NP, g = t / NP;
+    float acc[BS];
+#pragma unroll
+    for (int v = 0; v < BS; v++) acc[v] = 0.f;
+    if (g < G) {
+      const float4* w = Wt + i0 + i;
+#pragma unroll 4
+      for (int c = g; c < ncol; c += G) {
+        const float4 wv = w[(int64_t)c * nT];
+        float m[3][BS];
+        load_m<BS>(Ms + (int64_t)cols[c0 + c] * 3 * B + b0, B, nlive, vec, m);
+#pragma unroll
+        for (int v = 0; v < BS; v++) acc[v] = fmaf(wv.x, m[0][v], fmaf(wv.y, m[1][v], fmaf(wv.z, m[2][v], acc[v])));
+      }
+    }
+    __syncthreads();  // the previous pass's reduction has been read
+#pragma unroll
+    for (int v = 0; v < BS; v++) red[v * NS_THREADS + t] = acc[v];
+    __syncthreads();
+    for (int q = t; q < NP * BS; q += NS_THREADS) {
+      const int ii = q % NP, v = q / NP;
+      if (v < nlive) {
+        float sum = 0.f;
+        for (int gg = 0; gg < G; gg++) sum += red[v * NS_THREADS + gg * NP + ii];
+        u_s[(int64_t)(rT.z + i0 + ii) * B + b0 + v] += sum;
+      }
+    }
+  }
+}
+
+template <int BS>
+void launch_near_small(Plan& P, const float* Ms, int B, float* u_s, cudaStream_t s) {
+  dim3 grid((unsigned)P.h_p2p_targets.size(), (unsigned)((B + BS - 1) / BS));
+  k_near_apply32_s<BS><<<grid, NS_THREADS, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off32,
+                                                   P.W32, Ms, B, u_s);
+  DM_LAUNCH("k_near_apply32_s");
+}
+
 void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s) {
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
   if (!nT) return;
+  if (B < NEAR_SMALL_BATCH) {
+    if (B == 1)
+      launch_near_small<1>(P, Ms, B, u_s, s);
+    else if (B == 2)
+      launch_near_small<2>(P, Ms, B, u_s, s);
+    else if (B <= 4)
+      launch_near_small<4>(P, Ms, B, u_s, s);
+    else
+      launch_near_small<8>(P, Ms, B, u_s, s);
+    return;
+  }
   if (B % 4 == 0) {
     const size_t smem = sizeof(float4) * NB_WARPS * 2 * NB_CW * NB_NT;  // = the reduction area
     static bool attr3 = false;

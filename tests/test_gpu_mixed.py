@@ -85,13 +85,15 @@ def test_tensor_core_m2l_vs_fp64(prec, p, B):
 
 
 @pytest.mark.parametrize("p", [4, 6, 8])
-@pytest.mark.parametrize("B", [1, 3, 32, 40])
+@pytest.mark.parametrize("B", [1, 2, 3, 12, 32, 40])
 def test_table_m2l_vs_fp64(p, B):
     """Table-driven FP32 M2L on CUDA cores (the FP32 precision at every batch,
     the tensor-core precisions at small ones): one state per lane for B = 1
-    (32 sources per warp step), a ragged state slice for B = 3, a full 32-state
-    slice, and two slices with a ragged second one (B = 40).  The ball's octree
-    has leaves on several levels, so pairs with f_S != 1 are included."""
+    (32 sources per warp step), ragged state slices for B = 3 and 12, a full
+    32-state slice, and two slices with a ragged second one (B = 40).  The
+    ball's octree has leaves on several levels, so pairs with f_S != 1 are
+    included.  The same batches take the small-batch near-field kernel through
+    its vector (B = 1, 2, 32, 40) and masked (B = 3, 12) loads of M."""
     nodes, tets = inputs.sphere(h=0.13)
     M = inputs.gaussian_unit_m(nodes.shape[0], batch=B, seed=70 + B)
     p64 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=B, near_mode=1)
