@@ -37,6 +37,10 @@ WORKLOADS = {
     "sphere200k": dict(mesh="sphere", h="SPHERE_200K_H", p=8, theta=0.5, leaf=128),
     "cube8": dict(mesh="cube", n=8, p=4, theta=0.5, leaf=32),
     "sphere30k": dict(mesh="sphere", h=0.095, p=6, theta=0.5, leaf=32),
+    # many states on one larger ball: seeded unit vectors smoothed over 3 mesh-neighbour passes
+    "sphere500k": dict(mesh="sphere", h="SPHERE_500K_H", p=8, theta=0.5, leaf=128, M="smoothed"),
+    # 64 meshes of uneven size (10k-300k tets: cubes, balls, ellipsoids) in one submission
+    "multi64": dict(mesh="multi", n=64, p=8, theta=0.5, leaf=128, M="smoothed"),
 }
 
 
@@ -74,10 +78,18 @@ def make_mesh(w):
     return inputs.sphere(h=h)
 
 
-def make_M(nn, B, seed_offset=0):
+def make_M(nn, B, seed_offset=0, tets=None, w=None):
     from paper_1606_00247_gb300 import inputs
 
+    if w is not None and w.get("M") == "smoothed":
+        return inputs.smoothed_unit_m(tets, nn, batch=B, seed=inputs.MAG_SEED + 3 + seed_offset)
     return inputs.gaussian_unit_m(nn, seed=inputs.MAG_SEED + 1 + seed_offset, batch=B)
+
+
+def data_note(w):
+    shape = "seeded Delaunay ball" if w["mesh"] == "sphere" else w["mesh"]
+    mag = "unit nodal M smoothed over 3 neighbour passes" if w.get("M") == "smoothed" else "Gaussian unit nodal M"
+    return f"synthetic ({shape}, {mag})"
 
 
 # ---------------------------------------------------------------------------
@@ -196,8 +208,8 @@ NCU_TRAFFIC = {
 
 def m2l_on_tensor_cores(precision, B, table_batch):
     """The tensor-core precisions run the FP32 table M2L on CUDA cores up to
-    m2l_table_batch states (0: the library default of 16; < 0: never)."""
-    limit = 16 if table_batch == 0 else max(table_batch, 0)
+    m2l_table_batch states (0: the library default of 8; < 0: never)."""
+    limit = 8 if table_batch == 0 else max(table_batch, 0)
     return precision in ("tf32", "bf16x3", "bf16x6") and B > limit
 
 
@@ -307,13 +319,16 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     w = workload(args)
+    if w["mesh"] == "multi":
+        return run_multi(args, rank, world, local_rank, w)
     nodes, tets = make_mesh(w)
     B = args.batch
     plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
-                near_mode=args.near_mode, max_batch=B, device=dev, autotune=bool(args.autotune),
+                near_mode=args.near_mode, max_batch=B, device=dev, autotune=int(args.autotune),
                 m2l_table_batch=args.m2l_table_batch)
     st0 = plan.stats()
-    M = torch.as_tensor(make_M(nodes.shape[0], B, seed_offset=rank), device=dev)
+    w["leaf"] = st0["leaf_size"]  # the leaf kept by the leaf-size tuner (autotune bit 1), else the requested one
+    M = torch.as_tensor(make_M(nodes.shape[0], B, seed_offset=rank, tets=tets, w=w), device=dev)
     u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device=dev)
     H = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
@@ -342,7 +357,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms, value = aggregate_ranks(total_ms, B * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside)
-    Mh = make_M(nodes.shape[0], B, seed_offset=rank)
+    Mh = make_M(nodes.shape[0], B, seed_offset=rank, tets=tets, w=w)
     plan.eval_host(Mh)
     t_e2e = []
     for _ in range(args.steps):
@@ -353,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
 
     # live per-stage timing pass (CUDA events on the eval stream, inside the library)
     prof = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
-                near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=bool(args.autotune),
+                near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=int(args.autotune) & 1,
                 m2l_table_batch=args.m2l_table_batch)
     for _ in range(2):
         prof.eval(M, u, H)
@@ -415,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32",
-        "data": "synthetic (seeded Delaunay ball, Gaussian unit nodal M)",
+        "data": data_note(w),
         "config": {"workload": args.workload, "n_tets": st0["n_tets"], "n_nodes": st0["n_nodes"],
                    "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_gpu": B,
                    "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
@@ -424,7 +439,8 @@ def run_ours(args, rank, world, local_rank):
                    "plan_ms": st0["plan_ms"], "m2l_operators": st0["n_m2l_ops"],
                    "m2l_ring": {"targets_per_cta": st0["m2l_targets_per_cta"], "kps": st0["m2l_kps"],
                                 "bytes": st0["m2l_ring_bytes"],
-                                "autotuned": bool(args.autotune)}},
+                                "autotuned": bool(args.autotune & 1)},
+                   "leaf_tuned": bool(args.autotune & 2)},
         "roofline": roof,
         "fp64_reference": ref_info,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Mh.nbytes),
@@ -434,7 +450,124 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": wall,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_sample(nodes, tets, w, make_M(nodes.shape[0], 1)[0], budget_s=args.cpu_budget)
+        out["cpu_baseline"] = oracle_sample(nodes, tets, w, make_M(nodes.shape[0], 1, tets=tets, w=w)[0],
+                                            budget_s=args.cpu_budget)
+    return out
+
+
+def multi_meshes(w):
+    from paper_1606_00247_gb300 import inputs
+
+    return inputs.batch_meshes(n=w["n"])
+
+
+def run_multi(args, rank, world, local_rank, w):
+    """Meshes of uneven size, each with B states, through one submission
+    (demag_eval_multi: run once, recorded as a CUDA graph, replayed per step).
+    One evaluation = one state on one mesh."""
+    import torch
+
+    from paper_1606_00247_gb300.api import Plan, eval_multi_into
+
+    dev = torch.device(f"cuda:{local_rank}")
+    meshes = multi_meshes(w)
+    B = args.batch
+    kw = dict(p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision, near_mode=args.near_mode,
+              max_batch=B, device=dev, autotune=int(args.autotune) & 1, m2l_table_batch=args.m2l_table_batch)
+    t0 = time.perf_counter()
+    plans = [Plan(n, t, **kw) for n, t in meshes]
+    plan_s = time.perf_counter() - t0
+    Mh = [make_M(n.shape[0], B, seed_offset=rank + 17 * k, tets=t, w=w) for k, (n, t) in enumerate(meshes)]
+    Ms = [torch.as_tensor(m, device=dev) for m in Mh]
+    us = [torch.empty((B, n.shape[0]), dtype=torch.float64, device=dev) for n, _ in meshes]
+    Hs = [torch.empty((B, n.shape[0], 3), dtype=torch.float64, device=dev) for n, _ in meshes]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        eval_multi_into(plans, Ms, us, Hs)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        eval_multi_into(plans, Ms, us, Hs)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    per_sub = sum(pl.stats()["eval_launches"] for pl in plans)
+    total_ms, value = aggregate_ranks(total_ms, len(plans) * B * args.steps, world, dev)
+    # end to end: pinned host M in, u and H out, around the same submission
+    Mp = [torch.as_tensor(m).pin_memory() for m in Mh]
+    up = [torch.empty(u.shape, dtype=u.dtype).pin_memory() for u in us]
+    Hp = [torch.empty(H.shape, dtype=H.dtype).pin_memory() for H in Hs]
+    t_e2e = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        for d, h in zip(Ms, Mp):
+            d.copy_(h, non_blocking=True)
+        eval_multi_into(plans, Ms, us, Hs)
+        for h, d in zip(up + Hp, us + Hs):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t_e2e.append(time.perf_counter() - t1)
+    e2e_value = world * len(plans) * B * args.steps / sum(t_e2e)
+    # accuracy gate on the smallest, a median and the largest mesh: state 0 vs FP64
+    order = sorted(range(len(meshes)), key=lambda k: meshes[k][1].shape[0])
+    errs = []
+    if args.precision != "fp64" and not args.no_fp64_ref:
+        for k in (order[0], order[len(order) // 2], order[-1]):
+            n, t = meshes[k]
+            u64, H64 = Plan(n, t, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64", near_mode=1,
+                            max_batch=1, device=dev).eval(Ms[k][:1])
+            errs.append({"n_tets": int(t.shape[0]),
+                         "rel_l2_u": float(torch.linalg.norm(us[k][0] - u64[0]) / torch.linalg.norm(u64[0])),
+                         "rel_l2_H": float(torch.linalg.norm(Hs[k][0] - H64[0]) / torch.linalg.norm(H64[0]))})
+    # roofline of the dominant stage on the largest mesh, evaluated alone with stage timers
+    big = order[-1]
+    prof = Plan(meshes[big][0], meshes[big][1], profile=True, **kw)
+    prof.reset_timers()
+    nprof = max(2, min(args.steps, 5))
+    for _ in range(nprof):
+        flush.zero_()
+        prof.eval(Ms[big], us[big], Hs[big])
+    pst = prof.stats()
+    pst["_batch"] = B
+    pst["near_mode"] = args.near_mode
+    roof = roofline_for(pst, nprof, args.precision, measured_peaks(), clk.get("sm_mhz"),
+                        m2l_on_tensor_cores(args.precision, B, args.m2l_table_batch))
+    roof["scope"] = f"largest mesh of the submission ({meshes[big][1].shape[0]} tets), evaluated alone"
+    prof.close()
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": f"synthetic ({len(meshes)} meshes: Kuhn cubes, Delaunay balls and ellipsoids; "
+                "unit nodal M smoothed over 3 neighbour passes)",
+        "config": {"workload": args.workload, "n_meshes": len(meshes),
+                   "n_tets_total": int(sum(t.shape[0] for _, t in meshes)),
+                   "n_tets_min": int(meshes[order[0]][1].shape[0]), "n_tets_max": int(meshes[big][1].shape[0]),
+                   "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_mesh": B,
+                   "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}", "submission": "demag_eval_multi, replayed CUDA graph",
+                   "plan_s_total": plan_s},
+        "roofline": roof,
+        "accuracy_vs_fp64": errs,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(sum(m.nbytes for m in Mh)),
+                "d2h_bytes_per_step": int(sum(u.numel() * 8 + H.numel() * 8 for u, H in zip(us, Hs)))},
+        "gpu_launches": int(per_sub * args.steps),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        n, t = meshes[big]
+        out["cpu_baseline"] = oracle_sample(n, t, w, make_M(n.shape[0], 1, tets=t, w=w)[0], budget_s=args.cpu_budget)
     return out
 
 
@@ -442,8 +575,11 @@ def run_reference(args, rank):
     if rank != 0:
         return None
     w = workload(args)
-    nodes, tets = make_mesh(w)
-    M1 = make_M(nodes.shape[0], 1)[0]
+    if w["mesh"] == "multi":
+        nodes, tets = max(multi_meshes(w), key=lambda m: m[1].shape[0])
+    else:
+        nodes, tets = make_mesh(w)
+    M1 = make_M(nodes.shape[0], 1, tets=tets, w=w)[0]
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     first = oracle_sample(nodes, tets, w, M1, budget_s=budget)
     frac = None
@@ -515,7 +651,8 @@ def main():
     ap.add_argument("--near-mode", type=int, default=1)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-fp64-ref", action="store_true")
-    ap.add_argument("--autotune", type=int, default=1, help="1: time the M2L launch shapes at plan time")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="bit 0: time the M2L launch shapes at plan time; bit 1: also tune the leaf size")
     ap.add_argument("--m2l-table-batch", type=int, default=0,
                     help="largest batch run by the FP32 table M2L in the tensor-core precisions (0: default, -1: never)")
     ap.add_argument("--p", type=int, default=0)

@@ -68,11 +68,17 @@ typedef struct {
                              at plan time and applied at eval (Sec. 3.4 stores
                              the direct-interaction coefficients)            */
   int max_batch;       /* largest batch B a demag_eval will be given       */
-  int autotune;        /* 1: at plan time, time the launch shapes of the
-                             tensor-core M2L (TF32 / split BF16) on this
+  int autotune;        /* bit 0 (1): at plan time, time the launch shapes of
+                             the tensor-core M2L (TF32 / split BF16) on this
                              plan's own interaction lists and keep the
                              fastest (adds up to ~1 s to demag_plan_create);
-                             0: a fixed default shape                      */
+                             otherwise a fixed default shape.
+                          bit 1 (2): leaf size -- build the plan for
+                             leaf_size / 2, leaf_size, 2 leaf_size and
+                             4 leaf_size, time one evaluation of max_batch
+                             states on each and keep the fastest (up to four
+                             plan builds; demag_plan_stats reports the leaf
+                             kept).  0..3                                  */
   int profile;         /* 1: time every stage of demag_eval with CUDA events
                           on the eval stream (adds one synchronisation per
                           call); read with demag_plan_stats                  */
@@ -96,7 +102,7 @@ typedef struct {
                           FP32 on CUDA cores, from a per-plan table of the
                           translation derivatives (p in {4, 6, 8}); larger
                           batches use the tensor cores, whose tiles hold 128
-                          states.  0 = default (16), < 0 = never.  The FP32
+                          states.  0 = default (8), < 0 = never.  The FP32
                           precision always uses the table M2L when there is
                           one.                                              */
 } demag_options;

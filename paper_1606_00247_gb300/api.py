@@ -40,7 +40,7 @@ class Plan:
         opt.near_mode = int(near_mode)
         opt.max_batch = int(max_batch)
         opt.profile = int(bool(profile))
-        opt.autotune = int(bool(autotune))
+        opt.autotune = int(autotune)  # bit 0: M2L launch shape, bit 1: leaf size
         opt.m2l_targets_per_cta = int(m2l_targets_per_cta)
         opt.m2l_kps = int(m2l_kps)
         opt.m2l_promote = int(m2l_promote)

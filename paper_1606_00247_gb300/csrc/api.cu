@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" boundary of libdemag.so (include/demag.h).
 // No exception crosses it: every entry point catches and returns a status.
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -87,6 +88,116 @@ static void copy_convert(Dst* dst, const Src* src_dev, int64_t n, cudaStream_t s
   for (int64_t i = 0; i < n; i++) dst[i] = (Dst)h[i];
 }
 
+// leaf-size tuning: a fixed, smooth field of unit vectors (B x N_n x 3) to time evaluations with
+__global__ void k_tune_m(int64_t n, double* M) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = 0.37 * (double)(i % 9973), b = 0.11 * (double)(i % 7919);
+    M[3 * i] = sin(a) * cos(b);
+    M[3 * i + 1] = sin(a) * sin(b);
+    M[3 * i + 2] = cos(a);
+  }
+}
+
+static void release_plan(demag_plan_s* P) {
+  if (!P) return;
+  multi_forget_plan(P);
+  destroy_workspace(*P);
+  dfree_all(*P);
+  if (P->stream) cudaStreamDestroy(P->stream);
+  delete P;
+}
+
+static demag_plan_s* new_plan(const demag_options& o, int64_t n_nodes, int64_t n_tets, const double* nodes,
+                              const int32_t* tets) {
+  demag_plan_s* P = new demag_plan_s();
+  try {
+    P->opt = o;
+    P->p = o.p;
+    P->nc = ncoef_of(o.p);
+    P->nn = n_nodes;
+    P->nt = n_tets;
+    DM_CUDA(cudaGetDevice(&P->device));
+    DM_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    build_plan(*P, nodes, tets);
+  } catch (...) {
+    release_plan(P);
+    throw;
+  }
+  return P;
+}
+
+// device time of one evaluation of B states (after one untimed evaluation)
+static float time_eval(demag_plan_s* P, int B, const double* M, double* u, double* H) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  DM_CUDA(cudaEventCreate(&a));
+  DM_CUDA(cudaEventCreate(&b));
+  float ms = 0.f;
+  for (int k = 0; k < 3; k++) {
+    if (k == 1) DM_CUDA(cudaEventRecord(a, P->stream));
+    if (P->opt.precision == DEMAG_FP64)
+      eval_fp64(*P, M, B, u, H, P->stream);
+    else
+      eval_mixed(*P, M, B, u, H, P->stream);
+  }
+  DM_CUDA(cudaEventRecord(b, P->stream));
+  DM_CUDA(cudaEventSynchronize(b));
+  DM_CUDA(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / 2;
+}
+
+// autotune bit 1: build the plan for leaf sizes L/2, L, 2L, 4L (L = the
+// requested one), time an evaluation of max_batch states on each and keep the
+// fastest; the others are released as soon as they lose
+static demag_plan_s* tune_leaf(const demag_options& o, int64_t n_nodes, int64_t n_tets, const double* nodes,
+                               const int32_t* tets) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t nm = (int64_t)o.max_batch * n_nodes;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (size_t)(nm * 7)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DEMAG_ERR_OUT_OF_MEMORY, "leaf-size tuning buffers");
+  }
+  double *M = buf, *u = buf + 3 * nm, *H = buf + 4 * nm;
+  demag_plan_s* best = nullptr;
+  float best_ms = 0.f;
+  try {
+    k_tune_m<<<256, 256>>>(nm, M);
+    DM_CUDA(cudaGetLastError());
+    DM_CUDA(cudaDeviceSynchronize());
+    const int L = o.leaf_size;
+    for (int leaf : {std::max(1, L / 2), L, 2 * L, 4 * L}) {
+      demag_options oc = o;
+      oc.leaf_size = leaf;
+      demag_plan_s* P = new_plan(oc, n_nodes, n_tets, nodes, tets);
+      float ms = 0.f;
+      try {
+        ms = time_eval(P, o.max_batch, M, u, H);
+        destroy_workspace(*P);
+      } catch (...) {
+        release_plan(P);
+        throw;
+      }
+      if (!best || ms < best_ms) {
+        release_plan(best);
+        best = P;
+        best_ms = ms;
+      } else {
+        release_plan(P);
+      }
+    }
+  } catch (...) {
+    release_plan(best);
+    cudaFree(buf);
+    throw;
+  }
+  cudaFree(buf);
+  best->tuned_leaf_ms = best_ms;
+  best->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return best;
+}
+
 }  // namespace demag
 
 using namespace demag;
@@ -129,7 +240,7 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.leaf_size < 1) fail(DEMAG_ERR_INVALID_ARG, "leaf_size must be >= 1");
     if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
     if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
-    if (o.autotune != 0 && o.autotune != 1) fail(DEMAG_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o.autotune < 0 || o.autotune > 3) fail(DEMAG_ERR_INVALID_ARG, "autotune must be in 0..3");
     if (o.m2l_targets_per_cta < 0 || o.m2l_targets_per_cta > 2)
       fail(DEMAG_ERR_INVALID_ARG, "m2l_targets_per_cta must be 0, 1 or 2");
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
@@ -137,25 +248,12 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X6)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
-    P = new demag_plan_s();
-    P->opt = o;
-    P->p = o.p;
-    P->nc = ncoef_of(o.p);
-    P->nn = n_nodes;
-    P->nt = n_tets;
-    DM_CUDA(cudaGetDevice(&P->device));
-    DM_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
-    build_plan(*P, nodes, tets);
+    P = (o.autotune & 2) ? tune_leaf(o, n_nodes, n_tets, nodes, tets) : new_plan(o, n_nodes, n_tets, nodes, tets);
     if (o.theta >= 1.0)
       set_last_error("warning: theta >= 1, multipole expansions may not converge for accepted pairs");
     *out = P;
   });
-  if (st != DEMAG_OK && P) {
-    destroy_workspace(*P);
-    dfree_all(*P);
-    if (P->stream) cudaStreamDestroy(P->stream);
-    delete P;
-  }
+  if (st != DEMAG_OK && P) release_plan(P);
   return st;
 }
 

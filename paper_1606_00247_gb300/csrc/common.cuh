@@ -93,6 +93,7 @@ struct Plan {
   int64_t nn = 0, nt = 0;
   double lo[3] = {0, 0, 0}, side = 0, scale = 0;
   double plan_ms = 0;
+  float tuned_leaf_ms = 0;  // leaf-size tuning: device time of one evaluation of max_batch states
 
   // sorted geometry
   double* nodes_s = nullptr;      // nn x 3 (sorted node order)
@@ -296,7 +297,7 @@ bool launch_m2l32_tab(Plan& P, int B, const float* Q, float* L, cudaStream_t s);
 // largest batch for which the tensor-core precisions run the table-driven FP32
 // M2L instead of the tensor-core one (whose tiles hold 128 states)
 inline int m2l_table_batch(const Plan& P) {
-  return P.opt.m2l_table_batch < 0 ? 0 : (P.opt.m2l_table_batch == 0 ? 16 : P.opt.m2l_table_batch);
+  return P.opt.m2l_table_batch < 0 ? 0 : (P.opt.m2l_table_batch == 0 ? 8 : P.opt.m2l_table_batch);
 }
 // several plans in one submission (multi.cu); cached graphs of a plan are
 // dropped before the plan or its workspace goes away

@@ -112,8 +112,9 @@ SPHERE_500K_H = 0.0372
 def batch_meshes(n=64, min_tets=1e4, max_tets=3e5, seed=MESH_SEED + 4):
     """Meshes of uneven size for many-mesh submissions: target sizes
     log-uniform in [min_tets, max_tets], types round-robin Kuhn cube, ball,
-    ellipsoid with axis ratios (1, a, b), a, b ~ U[1, 4].  Ball and ellipsoid
-    spacings are scaled from the ball of 223,668 tets at SPHERE_200K_H."""
+    ellipsoid with axis ratios (1, a, b), a, b ~ U[1, 4] (a ball mesh stretched
+    by those factors).  Ball spacings are scaled from the ball of 223,668 tets
+    at SPHERE_200K_H."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(min_tets), np.log(max_tets), n))
     out = []
@@ -125,8 +126,8 @@ def batch_meshes(n=64, min_tets=1e4, max_tets=3e5, seed=MESH_SEED + 4):
         elif kind == 1:
             out.append(sphere(h=SPHERE_200K_H * (223668.0 / size) ** (1.0 / 3.0), seed=seed + i))
         else:
-            a, b = rng.uniform(1.0, 4.0, 2)
-            h = SPHERE_200K_H * (223668.0 * a * b / size) ** (1.0 / 3.0)
+            a, b = rng.uniform(1.0, 4.0, 2)  # the ball's mesh stretched: same tet count, elongated tets
+            h = SPHERE_200K_H * (223668.0 / size) ** (1.0 / 3.0)
             out.append(sphere(h=h, seed=seed + i, scale=(1.0, a, b)))
     return out
 
@@ -166,18 +167,21 @@ def landau_m(nodes, size=(2000.0, 1000.0), tilt=0.05, seed=MAG_SEED + 2):
 def smoothed_unit_m(tets, n_nodes, batch=1, passes=3, seed=MAG_SEED + 3):
     """iid unit vectors, then `passes` times M_i <- normalise(M_i + sum_{j~i} M_j)
     over mesh-edge neighbours."""
+    import scipy.sparse as sp
+
     rng = np.random.default_rng(seed)
     m = rng.standard_normal((batch, n_nodes, 3))
     m /= np.linalg.norm(m, axis=-1, keepdims=True)
     t = np.asarray(tets, dtype=np.int64)
     e = np.concatenate([t[:, [a, b]] for a in range(4) for b in range(a + 1, 4)], 0)
     e = np.unique(np.sort(e, axis=1), axis=0)
+    # I + adjacency of the mesh edges (each edge once, both directions)
+    A = sp.coo_matrix((np.ones(2 * len(e)), (np.r_[e[:, 0], e[:, 1]], np.r_[e[:, 1], e[:, 0]])),
+                      shape=(n_nodes, n_nodes)).tocsr() + sp.identity(n_nodes, format="csr")
     for _ in range(passes):
-        acc = m.copy()
-        np.add.at(acc, (slice(None), e[:, 0]), m[:, e[:, 1]])
-        np.add.at(acc, (slice(None), e[:, 1]), m[:, e[:, 0]])
+        acc = (A @ m.transpose(1, 0, 2).reshape(n_nodes, -1)).reshape(n_nodes, batch, 3).transpose(1, 0, 2)
         m = acc / np.linalg.norm(acc, axis=-1, keepdims=True)
-    return m
+    return np.ascontiguousarray(m)
 
 
 def random_tet(rng, scale=1.0, min_quality=0.05):

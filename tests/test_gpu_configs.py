@@ -10,7 +10,16 @@ bench lines):
   for the tensor-core M2L's accumulation.
 
 Both check the effect of promoting the leading M2L accumulator rows to FP32
-registers (the default): without it the film misses the 1e-4 bar."""
+registers (the default): without it the film misses the 1e-4 bar.
+
+Batched serving (many states on one mesh, many meshes in one submission):
+
+* the ball of 559,564 tets with 256 smoothed unit states (two 128-state
+  tensor-core tiles): sampled states of both tiles against FP64, and against
+  the same states evaluated as a batch of 2 (table-driven FP32 M2L);
+* 64 meshes of 10k-280k tets (cubes, balls, ellipsoids up to 1:4) with one state
+  each through one demag_eval_multi submission: every mesh bit-identical to its
+  own demag_eval, and the smallest, a median and the largest mesh against FP64."""
 import numpy as np
 import pytest
 import torch
@@ -72,3 +81,47 @@ def test_ball_uniform_m_tensor_core():
                     m2l_table_batch=tb).eval(M)
         for k in range(2):
             assert rel(u[k], u64[k]) <= bar and rel(H[k], H64[k]) <= bar, (prec, k)
+
+
+def test_ball500k_256_states():
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=inputs.SPHERE_500K_H)
+    assert tets.shape[0] == 559564
+    M = torch.as_tensor(inputs.smoothed_unit_m(tets, nodes.shape[0], batch=256), device="cuda")
+    u, H = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1, max_batch=256).eval(M)
+    pick = [0, 127, 128, 255]
+    Mp = M[pick].contiguous()
+    u64, H64 = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, near_mode=1, max_batch=4).eval(Mp)
+    for k, b in enumerate(pick):
+        assert rel(u[b], u64[k]) < 1e-5 and rel(H[b], H64[k]) < 1e-5, b
+    u2, H2 = Plan(nodes, tets, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1,
+                  max_batch=2).eval(M[[0, 255]].contiguous())
+    for k, b in enumerate((0, 255)):
+        assert rel(u2[k], u[b]) < 1e-5 and rel(H2[k], H[b]) < 1e-5, b
+
+
+def test_multi64_one_submission():
+    from paper_1606_00247_gb300.api import Plan, eval_multi_into
+
+    meshes = inputs.batch_meshes()
+    assert len(meshes) == 64
+    sizes = [t.shape[0] for _, t in meshes]
+    assert min(sizes) >= 10000 and max(sizes) <= 300000
+    plans = [Plan(n, t, p=8, leaf_size=128, theta=0.5, precision="bf16x3", near_mode=1, max_batch=1)
+             for n, t in meshes]
+    Ms = [torch.as_tensor(inputs.smoothed_unit_m(t, n.shape[0], seed=900 + k), device="cuda")
+          for k, (n, t) in enumerate(meshes)]
+    us = [torch.full((1, n.shape[0]), np.nan, dtype=torch.float64, device="cuda") for n, _ in meshes]
+    Hs = [torch.full((1, n.shape[0], 3), np.nan, dtype=torch.float64, device="cuda") for n, _ in meshes]
+    eval_multi_into(plans, Ms, us, Hs)  # direct run + graph recording
+    eval_multi_into(plans, Ms, us, Hs)  # replay
+    torch.cuda.synchronize()
+    for pl, M, u, H in zip(plans, Ms, us, Hs):
+        u1, H1 = pl.eval(M)
+        assert torch.equal(u, u1) and torch.equal(H, H1)
+    order = np.argsort(sizes)
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        n, t = meshes[k]
+        u64, H64 = Plan(n, t, p=8, leaf_size=128, theta=0.5, near_mode=1, max_batch=1).eval(Ms[k])
+        assert rel(us[k][0], u64[0]) < 1e-4 and rel(Hs[k][0], H64[0]) < 1e-4, sizes[k]

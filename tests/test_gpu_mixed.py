@@ -110,7 +110,7 @@ def test_table_m2l_vs_fp64(p, B):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_small_batch_tensor_precisions_use_the_table_m2l(prec):
-    """At batches up to m2l_table_batch (default 16) the tensor-core precisions
+    """At batches up to m2l_table_batch (default 8) the tensor-core precisions
     run the same FP32 kernels as the FP32 precision: identical bits."""
     nodes, tets = inputs.sphere(h=0.13)
     M = inputs.gaussian_unit_m(nodes.shape[0], batch=4, seed=91)
@@ -119,6 +119,20 @@ def test_small_batch_tensor_precisions_use_the_table_m2l(prec):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     c = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec, m2l_table_batch=-1).eval(M)
     assert not torch.equal(a[0], c[0])  # forced onto the tensor cores
+
+
+def test_leaf_size_tuner_keeps_one_of_the_candidates():
+    """autotune bit 1: plans for leaf L/2, L, 2L, 4L are timed on max_batch
+    states and the fastest is kept; its results equal a plan built directly
+    with that leaf."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=4, seed=93)
+    tuned = _plan(nodes, tets, p=6, leaf_size=32, max_batch=4, near_mode=1, precision="fp32", autotune=2)
+    leaf = tuned.stats()["leaf_size"]
+    assert leaf in (16, 32, 64, 128)
+    u, H = tuned.eval(M)
+    u1, H1 = _plan(nodes, tets, p=6, leaf_size=leaf, max_batch=4, near_mode=1, precision="fp32").eval(M)
+    assert torch.equal(u, u1) and torch.equal(H, H1)
 
 
 @pytest.mark.parametrize("scale", [1e-3, 1e3])
