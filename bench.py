@@ -328,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
                 m2l_table_batch=args.m2l_table_batch)
     st0 = plan.stats()
     w["leaf"] = st0["leaf_size"]  # the leaf kept by the leaf-size tuner (autotune bit 1), else the requested one
+    w["p"] = st0["p"]  # the order kept by the order tuner (autotune bit 2), else the requested one
     M = torch.as_tensor(make_M(nodes.shape[0], B, seed_offset=rank, tets=tets, w=w), device=dev)
     u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device=dev)
     H = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64, device=dev)
@@ -440,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
                    "m2l_ring": {"targets_per_cta": st0["m2l_targets_per_cta"], "kps": st0["m2l_kps"],
                                 "bytes": st0["m2l_ring_bytes"],
                                 "autotuned": bool(args.autotune & 1)},
-                   "leaf_tuned": bool(args.autotune & 2)},
+                   "leaf_tuned": bool(args.autotune & 2), "p_tuned": bool(args.autotune & 4)},
         "roofline": roof,
         "fp64_reference": ref_info,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Mh.nbytes),
@@ -652,7 +653,8 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--autotune", type=int, default=1,
-                    help="bit 0: time the M2L launch shapes at plan time; bit 1: also tune the leaf size")
+                    help="bit 0: time the M2L launch shapes at plan time; bit 1: tune the leaf size; "
+                         "bit 2: pick the smallest p meeting 5e-5 against FP64 p = 10")
     ap.add_argument("--m2l-table-batch", type=int, default=0,
                     help="largest batch run by the FP32 table M2L in the tensor-core precisions (0: default, -1: never)")
     ap.add_argument("--p", type=int, default=0)

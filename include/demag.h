@@ -78,7 +78,14 @@ typedef struct {
                              4 leaf_size, time one evaluation of max_batch
                              states on each and keep the fastest (up to four
                              plan builds; demag_plan_stats reports the leaf
-                             kept).  0..3                                  */
+                             kept).
+                          bit 2 (4): expansion order -- the smallest p in
+                             {4, 6, 8, 10} whose u and H on one synthetic
+                             state are within 5e-5 (rel-L2) of an FP64
+                             evaluation at p = 10 with the same leaf and
+                             theta; the p argument is then ignored and
+                             demag_plan_stats reports the p kept.  Applied
+                             before the leaf tuning.  0..7                 */
   int profile;         /* 1: time every stage of demag_eval with CUDA events
                           on the eval stream (adds one synchronisation per
                           call); read with demag_plan_stats                  */

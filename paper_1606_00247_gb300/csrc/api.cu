@@ -59,6 +59,16 @@ void StageClock::finish() {
 void dfree_all(Plan& P) {
   for (auto& b : P.bufs) cudaFree(b.ptr);
   P.bufs.clear();
+}
+
+void dfree(Plan& P, void* ptr) {
+  for (size_t i = 0; i < P.bufs.size(); i++)
+    if (P.bufs[i].ptr == ptr) {
+      cudaFree(ptr);
+      P.device_bytes -= (int64_t)P.bufs[i].bytes;
+      P.bufs.erase(P.bufs.begin() + (long)i);
+      return;
+    }
   P.device_bytes = 0;
 }
 
@@ -198,6 +208,83 @@ static demag_plan_s* tune_leaf(const demag_options& o, int64_t n_nodes, int64_t 
   return best;
 }
 
+// relative L2 distance of two device vectors of n doubles (host reduction, plan time only)
+static double rel_l2_dev(const double* a, const double* b, int64_t n) {
+  std::vector<double> ha(n), hb(n);
+  DM_CUDA(cudaMemcpy(ha.data(), a, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  DM_CUDA(cudaMemcpy(hb.data(), b, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  double num = 0.0, den = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    num += (ha[i] - hb[i]) * (ha[i] - hb[i]);
+    den += hb[i] * hb[i];
+  }
+  return den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
+}
+
+// autotune bit 2: the smallest p in {4, 6, 8, 10} whose u and H on one state are within
+// DEMAG_TUNE_P_TARGET (rel-L2) of an FP64 evaluation at p = 10 with the same leaf and theta
+// (the truncation error at p = 10 is ~1e-6 at theta = 0.5, two orders below the target)
+constexpr double DEMAG_TUNE_P_TARGET = 5e-5;
+
+static int tune_p(const demag_options& o, int64_t n_nodes, int64_t n_tets, const double* nodes,
+                  const int32_t* tets) {
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (size_t)(n_nodes * 11)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DEMAG_ERR_OUT_OF_MEMORY, "order tuning buffers");
+  }
+  double *M = buf, *u0 = buf + 3 * n_nodes, *H0 = buf + 4 * n_nodes, *u = buf + 7 * n_nodes, *H = buf + 8 * n_nodes;
+  int chosen = 10;
+  try {
+    k_tune_m<<<256, 256>>>(n_nodes, M);
+    DM_CUDA(cudaGetLastError());
+    DM_CUDA(cudaDeviceSynchronize());  // the plans evaluate on their own non-blocking streams
+    demag_options oc = o;
+    oc.max_batch = 1;
+    oc.autotune = 0;
+    oc.precision = DEMAG_FP64;
+    oc.p = 10;
+    demag_plan_s* R = new_plan(oc, n_nodes, n_tets, nodes, tets);
+    try {
+      eval_fp64(*R, M, 1, u0, H0, R->stream);
+      DM_CUDA(cudaStreamSynchronize(R->stream));
+    } catch (...) {
+      release_plan(R);
+      throw;
+    }
+    release_plan(R);
+    for (int p : {4, 6, 8}) {
+      oc = o;
+      oc.max_batch = 1;
+      oc.autotune = 0;
+      oc.p = p;
+      demag_plan_s* P = new_plan(oc, n_nodes, n_tets, nodes, tets);
+      double err = 0.0;
+      try {
+        if (oc.precision == DEMAG_FP64)
+          eval_fp64(*P, M, 1, u, H, P->stream);
+        else
+          eval_mixed(*P, M, 1, u, H, P->stream);
+        DM_CUDA(cudaStreamSynchronize(P->stream));
+        err = std::max(rel_l2_dev(u, u0, n_nodes), rel_l2_dev(H, H0, 3 * n_nodes));
+      } catch (...) {
+        release_plan(P);
+        throw;
+      }
+      release_plan(P);
+      if (err <= DEMAG_TUNE_P_TARGET) {
+        chosen = p;
+        break;
+      }
+    }
+  } catch (...) {
+    cudaFree(buf);
+    throw;
+  }
+  cudaFree(buf);
+  return chosen;
+}
+
 }  // namespace demag
 
 using namespace demag;
@@ -240,7 +327,7 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.leaf_size < 1) fail(DEMAG_ERR_INVALID_ARG, "leaf_size must be >= 1");
     if (!(o.theta > 0) || !std::isfinite(o.theta)) fail(DEMAG_ERR_INVALID_ARG, "theta must be finite and > 0");
     if (o.max_batch < 1) fail(DEMAG_ERR_INVALID_ARG, "max_batch must be >= 1");
-    if (o.autotune < 0 || o.autotune > 3) fail(DEMAG_ERR_INVALID_ARG, "autotune must be in 0..3");
+    if (o.autotune < 0 || o.autotune > 7) fail(DEMAG_ERR_INVALID_ARG, "autotune must be in 0..7");
     if (o.m2l_targets_per_cta < 0 || o.m2l_targets_per_cta > 2)
       fail(DEMAG_ERR_INVALID_ARG, "m2l_targets_per_cta must be 0, 1 or 2");
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
@@ -248,7 +335,14 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X6)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (o.autotune & 4) {
+      o.p = tune_p(o, n_nodes, n_tets, nodes, tets);
+      o.autotune &= ~4;
+    }
     P = (o.autotune & 2) ? tune_leaf(o, n_nodes, n_tets, nodes, tets) : new_plan(o, n_nodes, n_tets, nodes, tets);
+    if (opt && (opt->autotune & 6))
+      P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (o.theta >= 1.0)
       set_last_error("warning: theta >= 1, multipole expansions may not converge for accepted pairs");
     *out = P;

@@ -245,6 +245,7 @@ T* dalloc(Plan& P, size_t n) {
   return (T*)p;
 }
 void dfree_all(Plan& P);
+void dfree(Plan& P, void* ptr);  // one plan buffer, before the plan is destroyed
 
 // stages (defined in plan.cu / fmm.cu / p2p.cu / eval.cu)
 void build_plan(Plan& P, const double* nodes, const int32_t* tets);

@@ -307,15 +307,17 @@ void destroy_workspace(Plan& P) {
   P.ws = nullptr;
 }
 
+// sized for the largest batch evaluated so far (grown, never shrunk), so a plan
+// built for max_batch states holds only what its evaluations use
 Workspace& workspace(Plan& P, int B) {
-  int need = std::max(B, P.opt.max_batch);
+  const int need = B;
   if (P.ws && P.ws->B >= need) return *P.ws;
   destroy_workspace(P);
   Workspace* W = new Workspace();
   W->B = need;
   const size_t nn = P.nn, nt = P.nt, nc = P.nc, ncell = P.ncells;
   const bool mixed = P.opt.precision != DEMAG_FP64, otf = P.opt.near_mode == 0;
-  W->Ms = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
+  if (!mixed || otf) W->Ms = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);  // FP64 sorted M
   if (!mixed) {
     W->Q = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
     W->L = (double*)ws_alloc(*W, sizeof(double) * ncell * nc * need);
@@ -327,12 +329,9 @@ Workspace& workspace(Plan& P, int B) {
     const size_t qp = m2l_tc_pack_bytes(P, need);
     if (qp) W->QP = (unsigned char*)ws_alloc(*W, qp);
   }
-  W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);
+  if (!mixed || otf) W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);  // FP64 sorted u
   if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);
-  W->M_dev = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
-  W->u_dev = (double*)ws_alloc(*W, sizeof(double) * nn * need);
-  W->H_dev = (double*)ws_alloc(*W, sizeof(double) * nn * 3 * need);
-  W->err = (int*)ws_alloc(*W, sizeof(int));
+  W->err = (int*)ws_alloc(*W, sizeof(int));  // staging for host M, u, H: at the first host-pointer call
   P.ws = W;
   return *W;
 }
@@ -458,6 +457,12 @@ bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   *ud = u;
   *Hd = H;
   if (!dev) {
+    if (!W.M_dev) {
+      const size_t nn = P.nn, need = W.B;
+      W.M_dev = (double*)ws_alloc(W, sizeof(double) * nn * 3 * need);
+      W.u_dev = (double*)ws_alloc(W, sizeof(double) * nn * need);
+      W.H_dev = (double*)ws_alloc(W, sizeof(double) * nn * 3 * need);
+    }
     DM_CUDA(cudaMemcpyAsync(W.M_dev, M, sizeof(double) * P.nn * 3 * B, cudaMemcpyHostToDevice, s));
     *Md = W.M_dev;
     *ud = W.u_dev;

@@ -942,6 +942,7 @@ void build_m2l_tc(Plan& P, const M2lKeys& K) {
 
 size_t m2l_tc_pack_bytes(const Plan& P, int B) {
   if (!tc_enabled(P)) return 0;
+  if (B <= m2l_table_batch(P) && P.m2l_tab != nullptr) return 0;  // the table-driven M2L runs instead
   const TcLayout G = layout_of(P);
   const size_t nsb = (size_t)(B + TC_M - 1) / TC_M;
   return (size_t)P.ncells * nsb * G.KS * G.a_bytes;

@@ -63,7 +63,7 @@ __global__ void k_col_offsets(const uint64_t* __restrict__ keys, int64_t n, int6
     }
     off[c] = b;
   }
-  if (c < n) cols[c] = (int32_t)(keys[c] & 0xffffffffu);
+  if (cols && c < n) cols[c] = (int32_t)(keys[c] & 0xffffffffu);
 }
 
 constexpr int NB_CHUNK = 32;
@@ -457,9 +457,19 @@ __global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
 
 }  // namespace
 
+// Plan-time near field, in chunks of consecutive target leaves (at most
+// NEAR_KEYS_PER_CHUNK (target, source-node) candidates each) so that large
+// meshes never hold more than one chunk's keys and FP64 coefficients:
+//   pass 1 -- per chunk, the distinct source nodes (columns) of every target;
+//   pass 2 -- per chunk again, the columns written in place, the FP64
+//             coefficients integrated (k_near_build) and, on the mixed path,
+//             packed to the FP32 layout; only the FP64 path keeps W64.
+constexpr int64_t NEAR_KEYS_PER_CHUNK = int64_t(1) << 27;
+
 void build_near_field(Plan& P) {
   cudaStream_t s = P.stream;
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
+  const bool mixed = P.opt.precision != DEMAG_FP64;
   P.w_coloff = dalloc<int64_t>(P, nT + 1);
   P.w_off = dalloc<int64_t>(P, nT + 1);
   if (nT == 0) {
@@ -467,9 +477,14 @@ void build_near_field(Plan& P) {
     DM_CUDA(cudaMemsetAsync(P.w_off, 0, sizeof(int64_t), s));
     P.w_cols = dalloc<int32_t>(P, 1);
     P.W64 = dalloc<double>(P, 1);
-    if (P.opt.precision != DEMAG_FP64) P.W32 = dalloc<float>(P, 1);
+    if (mixed) {
+      P.w_off32 = dalloc<int64_t>(P, 1);
+      DM_CUDA(cudaMemsetAsync(P.w_off32, 0, sizeof(int64_t), s));
+      P.W32 = dalloc<float>(P, 4);
+    }
     return;
   }
+  // candidate keys per target: 4 per source tet of its P2P list
   std::vector<int64_t> koff(nT + 1, 0);
   for (int64_t ti = 0; ti < nT; ti++) {
     int32_t T = P.h_p2p_targets[ti];
@@ -478,63 +493,106 @@ void build_near_field(Plan& P) {
       int4 r = P.h_range[P.h_p2p_src[e]];
       n += 4ll * (r.y - r.x);
     }
+    if (n > NEAR_KEYS_PER_CHUNK) fail(DEMAG_ERR_UNSUPPORTED, "near field of one target leaf too large");
     koff[ti + 1] = koff[ti] + n;
   }
-  const int64_t nk = koff[nT];
-  if (nk > (int64_t)INT32_MAX) fail(DEMAG_ERR_UNSUPPORTED, "near field too large for the precomputed mode");
-  Tmp<int64_t> dkoff(nT + 1);
-  DM_CUDA(cudaMemcpyAsync(dkoff.p, koff.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  int64_t ncols = 0;
-  {
-    Tmp<uint64_t> keys(nk), keys_s(nk);
-    k_near_keys<<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.tets_s, dkoff.p,
-                                              keys.p);
+  std::vector<int64_t> chunk{0};
+  for (int64_t ti = 0; ti < nT; ti++)
+    if (koff[ti + 1] - koff[chunk.back()] > NEAR_KEYS_PER_CHUNK) chunk.push_back(ti);
+  chunk.push_back(nT);
+  int64_t max_keys = 0;
+  for (size_t c = 0; c + 1 < chunk.size(); c++) max_keys = std::max(max_keys, koff[chunk[c + 1]] - koff[chunk[c]]);
+  Tmp<uint64_t> keys(max_keys), keys_s(max_keys);
+  Tmp<int64_t> dkoff(nT + 1), doff(nT + 1);
+  Tmp<int> nu(1);
+  size_t tb = 0, tb2 = 0;
+  cub::DeviceRadixSort::SortKeys(nullptr, tb, keys.p, keys_s.p, (int)max_keys, 0, 64, s);
+  cub::DeviceSelect::Unique(nullptr, tb2, keys_s.p, keys.p, nu.p, (int)max_keys, s);
+  Tmp<char> temp(std::max(tb, tb2));
+  // the distinct columns of the targets [t0, t1), sorted by (target, node), in keys.p; returns their count
+  auto columns = [&](int64_t t0, int64_t t1) -> int64_t {
+    const int64_t nk = koff[t1] - koff[t0];
+    std::vector<int64_t> rel(t1 - t0 + 1);
+    for (int64_t t = t0; t <= t1; t++) rel[t - t0] = koff[t] - koff[t0];
+    DM_CUDA(cudaMemcpyAsync(dkoff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_near_keys<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
+                                                     P.tets_s, dkoff.p, keys.p);
     DM_LAUNCH("k_near_keys");
-    size_t tb = 0;
-    cub::DeviceRadixSort::SortKeys(nullptr, tb, keys.p, keys_s.p, (int)nk, 0, 64, s);
-    Tmp<char> temp(tb);
-    DM_CUDA(cub::DeviceRadixSort::SortKeys(temp.p, tb, keys.p, keys_s.p, (int)nk, 0, 64, s));
-    Tmp<int> nu(1);
-    size_t tb2 = 0;
-    cub::DeviceSelect::Unique(nullptr, tb2, keys_s.p, keys.p, nu.p, (int)nk, s);
-    Tmp<char> temp2(tb2);
-    DM_CUDA(cub::DeviceSelect::Unique(temp2.p, tb2, keys_s.p, keys.p, nu.p, (int)nk, s));
+    size_t t = tb;
+    DM_CUDA(cub::DeviceRadixSort::SortKeys(temp.p, t, keys.p, keys_s.p, (int)nk, 0, 64, s));
+    t = tb2;
+    DM_CUDA(cub::DeviceSelect::Unique(temp.p, t, keys_s.p, keys.p, nu.p, (int)nk, s));
     int hnu = 0;
     DM_CUDA(cudaMemcpyAsync(&hnu, nu.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
-    ncols = hnu;
-    P.w_cols = dalloc<int32_t>(P, std::max<int64_t>(ncols, 1));
-    k_col_offsets<<<(unsigned)((std::max<int64_t>(ncols, nT + 1) + 255) / 256), 256, 0, s>>>(keys.p, ncols, nT,
-                                                                                          P.w_coloff, P.w_cols);
+    return hnu;
+  };
+  // pass 1: column counts per target
+  std::vector<int64_t> hcol(nT + 1, 0);
+  for (size_t c = 0; c + 1 < chunk.size(); c++) {
+    const int64_t t0 = chunk[c], t1 = chunk[c + 1];
+    const int64_t nu_c = columns(t0, t1);
+    k_col_offsets<<<(unsigned)((std::max<int64_t>(nu_c, t1 - t0 + 1) + 255) / 256), 256, 0, s>>>(
+        keys.p, nu_c, t1 - t0, doff.p, nullptr);
     DM_LAUNCH("k_col_offsets");
+    std::vector<int64_t> o(t1 - t0 + 1);
+    DM_CUDA(cudaMemcpyAsync(o.data(), doff.p, o.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int64_t t = t0; t < t1; t++) hcol[t + 1] = hcol[t0] + o[t - t0 + 1];
   }
-  std::vector<int64_t> hcol(nT + 1), hw(nT + 1, 0);
-  DM_CUDA(cudaMemcpyAsync(hcol.data(), P.w_coloff, (nT + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  DM_CUDA(cudaStreamSynchronize(s));
+  const int64_t ncols = hcol[nT];
+  if (ncols > (int64_t)INT32_MAX) fail(DEMAG_ERR_UNSUPPORTED, "near field too large for the precomputed mode");
+  std::vector<int64_t> hw(nT + 1, 0), hw32(nT + 1, 0);
   for (int64_t ti = 0; ti < nT; ti++) {
     int4 r = P.h_range[P.h_p2p_targets[ti]];
     hw[ti + 1] = hw[ti] + (hcol[ti + 1] - hcol[ti]) * (int64_t)(r.w - r.z) * 3;
+    hw32[ti + 1] = hw32[ti] + (hcol[ti + 1] - hcol[ti]) * (int64_t)(r.w - r.z) * 4;
   }
   P.n_wcols = ncols;
   P.n_wentries = hw[nT];
+  P.w_cols = dalloc<int32_t>(P, std::max<int64_t>(ncols, 1));
+  DM_CUDA(cudaMemcpyAsync(P.w_coloff, hcol.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   DM_CUDA(cudaMemcpyAsync(P.w_off, hw.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  P.W64 = dalloc<double>(P, std::max<int64_t>(P.n_wentries, 1));
-  DM_CUDA(cudaMemsetAsync(P.W64, 0, std::max<int64_t>(P.n_wentries, 1) * sizeof(double), s));
-  k_near_build<<<(unsigned)nT, 128, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s, P.tets_s,
-                                            P.tet_geo, P.tet_grad, P.w_coloff, P.w_cols, P.w_off, P.W64);
-  DM_LAUNCH("k_near_build");
-  if (P.opt.precision != DEMAG_FP64) {
-    // FP32 copy, [col][node][4] per target leaf (16-byte entries for the TMA-staged apply)
-    std::vector<int64_t> hw32(nT + 1, 0);
-    for (int64_t ti = 0; ti < nT; ti++) hw32[ti + 1] = hw32[ti] + (hw[ti + 1] - hw[ti]) / 3 * 4;
+  if (mixed) {
     P.w_off32 = dalloc<int64_t>(P, nT + 1);
     DM_CUDA(cudaMemcpyAsync(P.w_off32, hw32.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     P.W32 = dalloc<float>(P, std::max<int64_t>(hw32[nT], 4));
-    k_pack_w32<<<(unsigned)nT, 256, 0, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_off, P.w_off32, P.W64,
-                                            P.W32);
-    DM_LAUNCH("k_pack_w32");
+    P.W64 = nullptr;
+  } else {
+    P.W64 = dalloc<double>(P, std::max<int64_t>(hw[nT], 1));
   }
-  DM_CUDA(cudaStreamSynchronize(s));
+  int64_t max_w = 0;
+  for (size_t c = 0; c + 1 < chunk.size(); c++) max_w = std::max(max_w, hw[chunk[c + 1]] - hw[chunk[c]]);
+  Tmp<double> wtmp(mixed ? max_w : 0);
+  // pass 2: columns in place, FP64 coefficients, FP32 copy
+  for (size_t c = 0; c + 1 < chunk.size(); c++) {
+    const int64_t t0 = chunk[c], t1 = chunk[c + 1];
+    const int64_t nu_c = columns(t0, t1);
+    k_col_offsets<<<(unsigned)((std::max<int64_t>(nu_c, t1 - t0 + 1) + 255) / 256), 256, 0, s>>>(
+        keys.p, nu_c, t1 - t0, doff.p, P.w_cols + hcol[t0]);
+    DM_LAUNCH("k_col_offsets");
+    double* W = P.W64;
+    const int64_t* woff = P.w_off + t0;
+    if (mixed) {  // chunk-relative offsets into the temporary FP64 block
+      std::vector<int64_t> rel(t1 - t0 + 1);
+      for (int64_t t = t0; t <= t1; t++) rel[t - t0] = hw[t] - hw[t0];
+      DM_CUDA(cudaMemcpyAsync(doff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      W = wtmp.p;
+      woff = doff.p;
+    }
+    DM_CUDA(cudaMemsetAsync(W + (mixed ? 0 : hw[t0]), 0, std::max<int64_t>(hw[t1] - hw[t0], 1) * sizeof(double), s));
+    k_near_build<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
+                                                     P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad, P.w_coloff + t0,
+                                                     P.w_cols, woff, W);
+    DM_LAUNCH("k_near_build");
+    if (mixed) {
+      // FP32 copy, [col][node][4] per target leaf (16-byte entries)
+      k_pack_w32<<<(unsigned)(t1 - t0), 256, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.w_coloff + t0, woff,
+                                                     P.w_off32 + t0, W, P.W32);
+      DM_LAUNCH("k_pack_w32");
+    }
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
 }
 
 void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s) {

@@ -69,7 +69,7 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
   const bool mixed = P.opt.precision != DEMAG_FP64, otf = P.opt.near_mode == 0;
   Workspace w;
   w.B = B;
-  w.Ms = c.take<double>(nn * 3 * B);
+  if (!mixed || otf) w.Ms = c.take<double>(nn * 3 * B);
   if (!mixed) {
     w.Q = c.take<double>(ncell * nc * B);
     w.L = c.take<double>(ncell * nc * B);
@@ -81,7 +81,7 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     const size_t qp = m2l_tc_pack_bytes(P, B);
     if (qp) w.QP = c.take<unsigned char>(qp);
   }
-  w.u_s = c.take<double>(nn * B);
+  if (!mixed || otf) w.u_s = c.take<double>(nn * B);
   if (otf) w.state = c.take<double>(nt * TET_STATE * B);
   w.err = c.take<int>(1);
   if (W) {

@@ -939,6 +939,15 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   P.h_p2p_src = std::move(h_p2p_src);
   if (P.opt.near_mode == 1) build_near_field(P);
   if (P.opt.precision != DEMAG_FP64) build_mixed_operators(P);
+  if (P.opt.precision != DEMAG_FP64 && P.opt.near_mode == 1) {
+    // the mixed path with stored near-field coefficients evaluates from FP32
+    // copies only: the FP64 per-tet geometry and P2M operator go
+    DM_CUDA(cudaStreamSynchronize(P.stream));
+    dfree(P, P.tet_geo);
+    dfree(P, P.tet_grad);
+    dfree(P, P.Ghat);
+    P.tet_geo = P.tet_grad = P.Ghat = nullptr;
+  }
   DM_CUDA(cudaStreamSynchronize(s));
   P.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -193,3 +193,69 @@ def random_tet(rng, scale=1.0, min_quality=0.05):
         edges = [np.linalg.norm(v[i] - v[j]) for i in range(4) for j in range(i + 1, 4)]
         if vol / max(edges) ** 3 > min_quality / 6.0 * 0.1:
             return v
+
+
+INCLUSION_SEED = 603
+GRADED_20M_H0 = 1.0 / 80.0
+
+
+def _lattice(lo, hi, h, rng, jitter=0.2):
+    """Jittered cubic lattice of spacing h over the box [lo, hi] (points inside it)."""
+    axes = [np.arange(lo[a] + 0.5 * h, hi[a], h) for a in range(3)]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
+    p = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    return p + rng.uniform(-jitter * h, jitter * h, size=p.shape)
+
+
+def graded_cube(h0=GRADED_20M_H0, n_incl=50, seed=INCLUSION_SEED):
+    """Unit cube with n_incl spherical inclusions refined 8x: point spacing h0
+    outside, h0/2 and h0/4 in two transition shells (1.5 h0 and 0.75 h0
+    thick), h0/8 inside each ball.  Centres U[0.1, 0.9]^3, radii U[0.02, 0.05],
+    rejection so balls plus shells are disjoint.  Jittered lattices per region,
+    the cube's boundary sampled on an unjittered face lattice of spacing h0,
+    Delaunay (scipy); tets with volume below 1e-6 (h0/8)^3 dropped.  Returns
+    (nodes, tets, centres, radii)."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    sa, sb = 0.75 * h0, 1.5 * h0
+    cen, rad = [], []
+    while len(cen) < n_incl:
+        c, r = rng.uniform(0.1, 0.9, 3), rng.uniform(0.02, 0.05)
+        if all(np.linalg.norm(c - c2) > r + r2 + 2 * (sa + sb) for c2, r2 in zip(cen, rad)):
+            cen.append(c)
+            rad.append(r)
+    cen, rad = np.array(cen), np.array(rad)
+    outer = rad + sa + sb
+    pts = []
+    # outside: spacing h0, away from every ball's outer shell and from the cube faces
+    p = _lattice((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), h0, rng)
+    p = p[np.all((p > 0.25 * h0) & (p < 1.0 - 0.25 * h0), axis=1)]
+    d = np.min(np.linalg.norm(p[:, None, :] - cen[None, :, :], axis=2) - outer[None, :], axis=1)
+    pts.append(p[d > 0.0])
+    # cube faces: unjittered lattice of spacing h0 on each face (the hull is the cube)
+    g = np.linspace(0.0, 1.0, int(round(1.0 / h0)) + 1)
+    U, V = np.meshgrid(g, g, indexing="ij")
+    for a in range(3):
+        for v in (0.0, 1.0):
+            f = np.zeros((U.size, 3))
+            f[:, a] = v
+            f[:, (a + 1) % 3] = U.ravel()
+            f[:, (a + 2) % 3] = V.ravel()
+            pts.append(f)
+    # per inclusion: ball at h0/8, shells at h0/4 and h0/2
+    for c, r in zip(cen, rad):
+        for h, r0, r1 in ((h0 / 8, 0.0, r), (h0 / 4, r, r + sa), (h0 / 2, r + sa, r + sa + sb)):
+            q = _lattice(c - r1, c + r1, h, rng)
+            dq = np.linalg.norm(q - c, axis=1)
+            pts.append(q[(dq >= r0) & (dq < r1)])
+    pts = np.unique(np.concatenate(pts, 0), axis=0)
+    tri = Delaunay(pts)
+    tets = tri.simplices.astype(np.int64)
+    a, b, c4, d4 = (pts[tets[:, k]] for k in range(4))
+    vol = np.einsum("ij,ij->i", b - a, np.cross(c4 - a, d4 - a)) / 6.0
+    tets = tets[np.abs(vol) >= 1e-6 * (h0 / 8) ** 3]
+    used = np.unique(tets)
+    remap = -np.ones(pts.shape[0], dtype=np.int64)
+    remap[used] = np.arange(used.shape[0])
+    return np.ascontiguousarray(pts[used]), remap[tets].astype(np.int32), cen, rad

@@ -17,6 +17,12 @@ Batched serving (many states on one mesh, many meshes in one submission):
 * the ball of 559,564 tets with 256 smoothed unit states (two 128-state
   tensor-core tiles): sampled states of both tiles against FP64, and against
   the same states evaluated as a batch of 2 (table-driven FP32 M2L);
+* the graded unit cube (22.1M tets, 3.27M nodes, 50 inclusions refined 8x), up to 32
+  iid unit states: the mixed path (split BF16, table-driven FP32 M2L at this
+  batch, leaf 64, batch chosen to fit 180 GB) against the FP64 GPU FMM (near field on the fly)
+  on state 0, and the FP64 GPU FMM against the oracle's direct sum on 16
+  sampled nodes (inside inclusions, in shells and outside) within the
+  truncation error;
 * 64 meshes of 10k-280k tets (cubes, balls, ellipsoids up to 1:4) with one state
   each through one demag_eval_multi submission: every mesh bit-identical to its
   own demag_eval, and the smallest, a median and the largest mesh against FP64."""
@@ -125,3 +131,56 @@ def test_multi64_one_submission():
         n, t = meshes[k]
         u64, H64 = Plan(n, t, p=8, leaf_size=128, theta=0.5, near_mode=1, max_batch=1).eval(Ms[k])
         assert rel(us[k][0], u64[0]) < 1e-4 and rel(Hs[k][0], H64[0]) < 1e-4, sizes[k]
+
+
+def test_graded_20m(orc):
+    import time
+
+    from paper_1606_00247_gb300.api import Plan
+
+    t0 = time.perf_counter()
+    nodes, tets, cen, rad = inputs.graded_cube()
+    t_mesh = time.perf_counter() - t0
+    nn = nodes.shape[0]
+    assert 20e6 < tets.shape[0] < 24e6 and 3.0e6 < nn < 3.6e6
+    M = inputs.gaussian_unit_m(nn, batch=32, seed=inputs.MAG_SEED + 5)
+    # FP64 reference on state 0 first (near field integrated on the fly: no stored coefficients)
+    p64 = Plan(nodes, tets, p=8, leaf_size=64, theta=0.5, precision="fp64", near_mode=0, max_batch=1)
+    u64, H64 = p64.eval(torch.as_tensor(M[:1], device="cuda"))
+    u64, H64 = u64.cpu(), H64.cpu()
+    p64.close()
+    del p64
+    torch.cuda.empty_cache()
+    pl = Plan(nodes, tets, p=8, leaf_size=64, theta=0.5, precision="bf16x3", near_mode=1, max_batch=32,
+              m2l_table_batch=32)
+    st = pl.stats()
+    # the batch: the largest power of two (at most 32) whose workspace and inputs/outputs fit in
+    # 180 GB with the plan (FP32 moments and locals per cell, FP32 and FP64 node arrays per state)
+    per_state = st["n_cells"] * 165 * 4 * 2 + nn * (3 * 4 + 4) + nn * (3 * 8 + 8 + 3 * 8)
+    B = 32
+    while B > 1 and st["device_bytes"] + B * per_state > 175e9:
+        B //= 2
+    Md = torch.as_tensor(M[:B], device="cuda")
+    t1 = time.perf_counter()
+    u, H = pl.eval(Md)
+    torch.cuda.synchronize()
+    t_eval = time.perf_counter() - t1
+    free, total = torch.cuda.mem_get_info()
+    print(f"graded: mesh {t_mesh:.0f} s, plan {st['plan_ms'] / 1e3:.0f} s, plan {st['device_bytes'] / 1e9:.1f} GB, "
+          f"B = {B}, device in use {(total - free) / 1e9:.1f} GB, first eval {t_eval:.2f} s, "
+          f"cells {st['n_cells']}, M2L pairs {st['n_m2l']}")
+    assert B >= 8
+    assert total - free < 180e9  # plan, workspace for B states, inputs and outputs
+    u0, H0 = u[0].cpu(), H[0].cpu()
+    assert rel(u0, u64[0]) < 1e-4 and rel(H0, H64[0]) < 1e-4
+    # FP64 FMM vs the direct sum on sampled nodes: 6 inside inclusions, 5 in shells, 5 outside
+    d = np.full(nn, np.inf)
+    for c, r in zip(cen, rad):
+        d = np.minimum(d, np.linalg.norm(nodes - c, axis=1) - r)
+    rng = np.random.default_rng(7)
+    pick = np.concatenate([rng.choice(np.where(d < -0.005)[0], 6, replace=False),
+                           rng.choice(np.where((d > 0.001) & (d < 0.02))[0], 5, replace=False),
+                           rng.choice(np.where(d > 0.05)[0], 5, replace=False)])
+    ref = orc.direct(nodes, tets, M[0], targets=pick)
+    g = u64[0].numpy()[pick]
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-4

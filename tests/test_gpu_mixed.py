@@ -135,6 +135,27 @@ def test_leaf_size_tuner_keeps_one_of_the_candidates():
     assert torch.equal(u, u1) and torch.equal(H, H1)
 
 
+def test_order_tuner_picks_the_smallest_order_meeting_the_target():
+    """autotune bit 2: the smallest p in {4, 6, 8, 10} within 5e-5 of FP64 at
+    p = 10 on the tuner's own state.  The kept p meets the bar on other states
+    too, the next lower order does not come close, and a plan built directly
+    with the kept p gives the same results."""
+    nodes, tets = inputs.sphere(h=0.13)
+    M = inputs.gaussian_unit_m(nodes.shape[0], batch=2, seed=95)
+    tuned = _plan(nodes, tets, p=4, leaf_size=32, max_batch=2, near_mode=1, precision="fp32", autotune=4)
+    p = tuned.stats()["p"]
+    assert p in (4, 6, 8, 10)
+    u, H = tuned.eval(M)
+    u1, H1 = _plan(nodes, tets, p=p, leaf_size=32, max_batch=2, near_mode=1, precision="fp32").eval(M)
+    assert torch.equal(u, u1) and torch.equal(H, H1)
+    u10, H10 = _plan(nodes, tets, p=10, leaf_size=32, max_batch=2, near_mode=1).eval(M)
+    u10, H10 = u10.cpu().numpy(), H10.cpu().numpy()
+    assert per_state(u.cpu().numpy(), u10) < 1e-4 and per_state(H.cpu().numpy(), H10) < 1e-4
+    if p > 4:
+        ul, Hl = _plan(nodes, tets, p=p - 2, leaf_size=32, max_batch=2, near_mode=1, precision="fp32").eval(M)
+        assert max(per_state(ul.cpu().numpy(), u10), per_state(Hl.cpu().numpy(), H10)) > 2e-5
+
+
 @pytest.mark.parametrize("scale", [1e-3, 1e3])
 def test_mixed_scale_invariance(orc, scale):
     """Per-level scaling keeps FP32 in range for any mesh size."""
