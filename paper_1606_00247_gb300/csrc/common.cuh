@@ -172,6 +172,8 @@ struct Plan {
   int32_t* m2l_op = nullptr;        // n_m2l
   float* m2l_tab = nullptr;         // n_tc_ops x nc: FP32 b_k(v) per key (CUDA-core M2L)
   int32_t* m2l_tab_opdl = nullptr;  // n_m2l: key index | (level difference & 255) << 24
+  uint32_t* m2l_rc_items = nullptr; // row-chunk items (m | c << 16), then per row a CSR of its items
+  int m2l_rc_nitems = 0, m2l_rc_ch = 0;
   int tc_nt = 1, tc_kps = 0, tc_budget = 0;  // M2L launch shape: targets per CTA, k-steps per slot, ring bytes
   int tc_l3 = 0;                    // split BF16: k-steps in three limbs (0 = none, 99 = all)
   int tc_prom_group = 0, tc_prom_rows = 16;  // accumulator promotion: sources per group (0 = off), rows

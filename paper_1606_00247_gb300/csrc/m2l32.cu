@@ -11,7 +11,6 @@
 // b_k(v), computed in the block by the Taylor-coefficient recurrence of 1/|x|).
 // All threads run the same short loop (no per-warp code paths).
 #include <algorithm>
-#include <utility>
 
 #include "common.cuh"
 
@@ -172,283 +171,250 @@ bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaS
 
 
 // ---------------------------------------------------------------------------
-// Table-driven FP32 M2L for small batches (k_m2l32_tab).
+// Table-driven FP32 M2L for small batches (k_m2l32_rc).
 //
 // The same sum, with b_k(v_S) read from a per-plan table: one row of nc FP32
 // values per distinct translation key (dl, lattice offset), keyed as for the
-// tensor-core M2L, so each pair costs a table row instead of the recurrence.
-// Two facts shape the work.  Qt_0 = 0 (the degree-0 moment vanishes: P2M
-// integrates gradients of the monomials), so n runs over degrees 1 .. p - |m|
-// and the rows of degree p stay zero.  And the entries with |m| = tm, |n| = tn
-// form a dense cnt(tm) x cnt(tn) block (cnt(t) = (t+1)(t+2)/2) whose values
-// are the b_k of degree tm + tn: within a degree, the graded position of
-// m + n is J(J+1)/2 + C with J = j_m + j_n, C = c_m + c_n (j = b + c).
+// tensor-core M2L, so a pair costs a table row instead of the recurrence.
+// Qt_0 = 0 (the degree-0 moment vanishes: P2M integrates gradients of the
+// monomials), so n runs over 1 <= n < C(p - |m| + 3, 3) and the rows of degree
+// p have no terms.
 //
-// Layout: one CTA per (target, slice of SB states), SB = the batch rounded up
-// to a power of two, at most 32.  Lane = (source slot j, state b), so a warp
-// covers 32/SB sources at once and needs no broadcast between lanes.  Each
-// warp owns a fixed set of row degrees (assigned at compile time, balanced on
-// FMA count), keeps their accumulators in registers over all sources of the
-// target, and runs its blocks fully unrolled with every multi-index position
-// a compile-time constant: ~0.4 shared-memory loads per FMA.  Sources are
-// staged 32/SB at a time (cp.async, two buffers; rows of odd length so the 32
-// lanes' reads fall in distinct banks); f_S^|n| is applied to the staged
-// moments of sources on another level.  At the end the lanes of a state add
-// their per-source partial sums by a fixed shuffle tree, so results do not
-// depend on timing.
-namespace tab {
+// Thread = work item (row m, chunk c of CH consecutive n in the graded order):
+// it owns the accumulators of row m for the SB <= 8 states of its slice and
+// adds, over every source of the target, b_{m+n} f^|n| Qt_n for the n of its
+// chunk.  The CH table positions of b_{m+n} are computed once and held in
+// registers; items are ordered chunk-major, so the lanes of a warp read the
+// same moments (shared-memory broadcast, SB states as float4s) and gather b
+// from one table row.  No position is a compile-time constant, so the code is
+// small: a fully unrolled variant with one source per lane and compile-time
+// positions was bound by instruction fetch (~16 KB of straight-line code per
+// warp).  KS = 8 sources are staged per step by eight warps (cp.async, two
+// buffers, each warp's next two sources prefetched in registers); f_S^|n| is
+// applied in shared memory to the staged moments of sources on another level.
+// The chunks of a row are added in a fixed order at the end, so results do
+// not depend on timing.
+namespace rc {
 
-__host__ __device__ constexpr int cnt(int t) { return (t + 1) * (t + 2) / 2; }
-__host__ __device__ constexpr int tri(int t) { return t * (t + 1) * (t + 2) / 6; }
-__host__ __device__ constexpr int work(int p, int tm) { return cnt(tm) * (tri(p - tm + 1) - 1); }
-__host__ __device__ constexpr int band_j(int r) {
-  int j = 0;
-  while ((j + 1) * (j + 2) / 2 <= r) j++;
-  return j;
-}
-// position within degree tm + tn of (i-th multi-index of degree tm) + (j-th of degree tn)
-__host__ __device__ constexpr int band_sum(int i, int j) {
-  const int ji = band_j(i), jj = band_j(j);
-  const int J = ji + jj, C = (i - ji * (ji + 1) / 2) + (j - jj * (jj + 1) / 2);
-  return J * (J + 1) / 2 + C;
-}
+constexpr int KS = 8;  // sources per step
 
-constexpr int MAXR = 4, MAXBLK = 24, MAXDEG = 12;
-
-struct Roles {
-  int nblk[MAXR] = {}, tm[MAXR][MAXBLK] = {}, tn[MAXR][MAXBLK] = {}, aoff[MAXR][MAXBLK] = {};
-  int nacc[MAXR] = {}, ndeg[MAXR] = {}, deg[MAXR][MAXDEG] = {}, dacc[MAXR][MAXDEG] = {}, load[MAXR] = {};
-};
-
-// row degrees 0 .. p-1 to nr warps, heaviest first onto the least loaded warp;
-// blocks ordered by column degree, then row degree
-__host__ __device__ constexpr Roles make_roles(int p, int nr) {
-  Roles R{};
-  bool used[MAXDEG] = {};
-  for (int it = 0; it < p; it++) {
-    int best = -1;
-    for (int t = 0; t < p; t++)
-      if (!used[t] && (best < 0 || work(p, t) > work(p, best))) best = t;
-    used[best] = true;
-    int r = 0;
-    for (int q = 1; q < nr; q++)
-      if (R.load[q] < R.load[r]) r = q;
-    R.load[r] += work(p, best);
-    R.deg[r][R.ndeg[r]++] = best;
-  }
-  for (int r = 0; r < nr; r++) {
-    for (int a = 1; a < R.ndeg[r]; a++)
-      for (int b = a; b > 0 && R.deg[r][b - 1] > R.deg[r][b]; b--) {
-        const int t = R.deg[r][b];
-        R.deg[r][b] = R.deg[r][b - 1];
-        R.deg[r][b - 1] = t;
-      }
-    for (int d = 0; d < R.ndeg[r]; d++) {
-      R.dacc[r][d] = R.nacc[r];
-      R.nacc[r] += cnt(R.deg[r][d]);
+// (m, c) items of order p with chunk length ch, chunk-major: m | c << 16
+std::vector<uint32_t> items(int p, int ch) {
+  std::vector<uint32_t> it;
+  const int nc = ncoef_of(p);
+  for (int c = 0; c * ch < nc; c++)
+    for (int m = 0; m < nc; m++) {
+      int a, b, z;
+      mi_decode(m, a, b, z);
+      const int t = a + b + z, nmax = t < p ? ncoef_of(p - t) : 0;  // n < nmax, n >= 1
+      const int lo = std::max(1, c * ch), hi = std::min(nmax, (c + 1) * ch);
+      if (lo < hi) it.push_back((uint32_t)m | ((uint32_t)c << 16));
     }
-    for (int tn = 1; tn <= p; tn++)
-      for (int d = 0; d < R.ndeg[r]; d++)
-        if (R.deg[r][d] + tn <= p) {
-          const int k = R.nblk[r]++;
-          R.tm[r][k] = R.deg[r][d];
-          R.tn[r][k] = tn;
-          R.aoff[r][k] = R.dacc[r][d];
-        }
-  }
-  return R;
-}
-
-template <int V>
-struct C_ {
-  static constexpr int v = V;
-};
-
-// one dense block, column-major so consecutive FMAs go to different accumulators.
-// f_S^tn is applied to whichever side is shorter: the cnt(tn) moments, or the
-// cnt(tm) partial sums (these in R interleaved partials when cnt(tm) is small,
-// to keep the dependent chains short).
-template <int TM, int TN, int AOFF, int NA, int... IJ>
-__device__ __forceinline__ void block_fmas(float (&acc)[NA], const float* __restrict__ bs,
-                                           const float* __restrict__ qs, float fs, std::integer_sequence<int, IJ...>) {
-  constexpr int CM = cnt(TM), CN = cnt(TN), BT = tri(TM + TN), QT = tri(TN);
-  if constexpr (CM >= CN) {
-    float q[CN];
-#pragma unroll
-    for (int j = 0; j < CN; j++) q[j] = qs[(QT + j) * 32] * fs;
-    ((acc[AOFF + IJ % CM] = fmaf(bs[C_<BT + band_sum(IJ % CM, IJ / CM)>::v], q[IJ / CM], acc[AOFF + IJ % CM])), ...);
-  } else {
-    constexpr int R = CM == 1 ? 4 : (CM <= 3 ? 2 : 1);
-    float t[CM * R];
-#pragma unroll
-    for (int i = 0; i < CM * R; i++) t[i] = 0.f;
-    ((t[(IJ % CM) * R + (IJ / CM) % R] = fmaf(bs[C_<BT + band_sum(IJ % CM, IJ / CM)>::v], qs[(QT + IJ / CM) * 32],
-                                              t[(IJ % CM) * R + (IJ / CM) % R])),
-     ...);
-#pragma unroll
-    for (int i = 0; i < CM; i++) {
-      float s = t[i * R];
-#pragma unroll
-      for (int r = 1; r < R; r++) s += t[i * R + r];
-      acc[AOFF + i] = fmaf(fs, s, acc[AOFF + i]);
-    }
-  }
-}
-
-template <int P, int NR, int R, int BI, int NA>
-__device__ __forceinline__ void role_blocks(float (&acc)[NA], const float* __restrict__ bs,
-                                            const float* __restrict__ qs, const float (&fp)[P + 1]) {
-  constexpr Roles RT = make_roles(P, NR);
-  if constexpr (BI < RT.nblk[R]) {
-    constexpr int TM = RT.tm[R][BI], TN = RT.tn[R][BI];
-    block_fmas<TM, TN, RT.aoff[R][BI]>(acc, bs, qs, fp[TN], std::make_integer_sequence<int, cnt(TM) * cnt(TN)>{});
-    role_blocks<P, NR, R, BI + 1>(acc, bs, qs, fp);
-  }
-}
-
-// the target's rows of degree DEG(role, D): scale, sign and store
-template <int P, int NR, int R, int D, int NA>
-__device__ __forceinline__ void role_store(const float (&acc)[NA], float inv, float* L, int64_t row0, int B) {
-  constexpr Roles RT = make_roles(P, NR);
-  if constexpr (D < RT.ndeg[R]) {
-    constexpr int TM = RT.deg[R][D], A0 = RT.dacc[R][D];
-    const float sg = (TM & 1) ? -inv : inv;
-#pragma unroll
-    for (int i = 0; i < cnt(TM); i++) L[(row0 + tri(TM) + i) * B] = sg * acc[A0 + i];
-    role_store<P, NR, R, D + 1>(acc, inv, L, row0, B);
-  }
-}
-
-struct Ctx {
-  const int32_t* src;
-  const int32_t* opdl;  // per pair: key index | (dl & 255) << 24
-  const float* tab;
-  const float* Q;
-  int64_t e0, e1;
-  int B, b0, SB, lsb, NJ, nsteps;
-};
-
-// a lane's source for one step: slot j = lane >> lsb
-struct Meta {
-  int32_t S, opdl;
-  bool valid;
-};
-
-__device__ __forceinline__ Meta load_meta(const Ctx& c, int s, int lane) {
-  Meta m;
-  const int64_t e = c.e0 + (int64_t)s * c.NJ + (lane >> c.lsb);
-  m.valid = s < c.nsteps && e < c.e1;
-  m.S = m.valid ? c.src[e] : 0;
-  m.opdl = m.valid ? c.opdl[e] : 0;
-  return m;
+  return it;
 }
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cta_sync(int nthreads) { asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory"); }
-
-// stage one step into buf: NJ operator rows of RS floats (slot j at j RS), then
-// the moments as nc rows of 32 lanes (n at NJ RS + 32 n, lane j SB + b).  Warp
-// w copies the operator rows of slots w, w + NR, ...; every lane copies its own
-// moments for n = w, w + NR, ...  The slots' keys come from the lanes that own
-// them (lane j SB).
-template <int P, int NR>
-__device__ __forceinline__ void stage(const Ctx& c, const Meta& m, float* buf, int warp, int lane) {
-  constexpr int NC = tri(P + 1), RS = NC | 1;
-  for (int j = warp; j < c.NJ; j += NR) {
-    const int opdl = __shfl_sync(0xffffffffu, m.opdl, j << c.lsb);
-    const bool valid = __shfl_sync(0xffffffffu, (int)m.valid, j << c.lsb) != 0;
-    float* brow = buf + j * RS;
-    if (valid) {
-      const float* trow = c.tab + (int64_t)(opdl & 0xFFFFFF) * NC;
-      for (int k = lane; k < NC; k += 32) cp_async4(brow + k, trow + k);
-    } else {
-      for (int k = lane; k < NC; k += 32) brow[k] = 0.f;
-    }
-  }
-  float* qcol = buf + c.NJ * RS + lane;
-  const int b = lane & (c.SB - 1);
-  if (m.valid && c.b0 + b < c.B) {
-    const float* q = c.Q + (int64_t)m.S * NC * c.B + c.b0 + b;
-    for (int n = warp; n < NC; n += NR) cp_async4(qcol + 32 * n, q + (int64_t)n * c.B);
-  } else {
-    for (int n = warp; n < NC; n += NR) qcol[32 * n] = 0.f;
-  }
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-template <int P, int NR, int R>
-__device__ __forceinline__ void role_run(const Ctx& c, float* sm, float* L, int32_t T, float inv) {
-  constexpr int NC = tri(P + 1), RS = NC | 1;
-  constexpr Roles RT = make_roles(P, NR);
-  constexpr int NA = RT.nacc[R] > 0 ? RT.nacc[R] : 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bufsz = c.NJ * RS + 32 * NC;
-  float acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; i++) acc[i] = 0.f;
-  Meta cur = load_meta(c, 0, lane);
-  Meta nxt = load_meta(c, 1, lane);
-  stage<P, NR>(c, cur, sm, warp, lane);
-  cp_async_commit();
-  const int j = lane >> c.lsb;
-  for (int s = 0; s < c.nsteps; s++) {
-    cp_async_wait_all();
-    cta_sync(32 * NR);  // step s staged; step s - 1 consumed by every warp
-    const float* buf = sm + (s & 1) * bufsz;
-    if (s + 1 < c.nsteps) stage<P, NR>(c, nxt, sm + ((s + 1) & 1) * bufsz, warp, lane);
-    cp_async_commit();
-    const Meta after = load_meta(c, s + 2, lane);  // consumed by the next step's staging
-    // f_S^t = 2^(dl t), exact powers of two
-    float fp[P + 1];
-    fp[0] = 1.f;
-    fp[1] = ldexpf(1.f, cur.opdl >> 24);
-#pragma unroll
-    for (int t = 2; t <= P; t++) fp[t] = fp[t - 1] * fp[1];
-    role_blocks<P, NR, R, 0>(acc, buf + j * RS, buf + c.NJ * RS + lane, fp);
-    cur = nxt;
-    nxt = after;
-  }
-  // sum over the source slots of each state (lanes b, b + SB, ...)
-  for (int o = c.SB; o < 32; o <<= 1) {
-#pragma unroll
-    for (int i = 0; i < NA; i++) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-  }
-  if (lane < c.SB && c.b0 + lane < c.B) role_store<P, NR, R, 0>(acc, inv, L + c.b0 + lane, (int64_t)T * NC, c.B);
+// one buffer: KS operator rows (nc floats), KS moment blocks (nc x SB floats), KS level differences
+template <int SB>
+__host__ __device__ constexpr size_t buf_floats(int nc) {
+  return (size_t)KS * nc * (1 + SB) + KS;
 }
 
-template <int P, int NR>
-__global__ void __launch_bounds__(32 * NR) k_m2l32_tab(const int32_t* __restrict__ targets,
-                                                       const int64_t* __restrict__ m2l_off,
-                                                       const int32_t* __restrict__ m2l_src,
-                                                       const int32_t* __restrict__ m2l_opdl,
-                                                       const float* __restrict__ tab,
-                                                       const int32_t* __restrict__ level, double side, int B,
-                                                       int lsb, const float* __restrict__ Q, float* L) {
+template <int CH, int SB>
+__global__ void __launch_bounds__(1024) k_m2l32_rc(const int32_t* __restrict__ targets,
+                                                   const int64_t* __restrict__ m2l_off,
+                                                   const int32_t* __restrict__ m2l_src,
+                                                   const int32_t* __restrict__ m2l_opdl,
+                                                   const float* __restrict__ tab, const uint32_t* __restrict__ items,
+                                                   int nitems, const int32_t* __restrict__ level, double side, int p,
+                                                   int nc, int B, const float* __restrict__ Q, float* L) {
   extern __shared__ __align__(16) float sm[];
   const int32_t T = targets[blockIdx.x];
-  Ctx c;
-  c.src = m2l_src;
-  c.opdl = m2l_opdl;
-  c.tab = tab;
-  c.Q = Q;
-  c.e0 = m2l_off[T];
-  c.e1 = m2l_off[T + 1];
-  c.B = B;
-  c.lsb = lsb;
-  c.SB = 1 << lsb;
-  c.NJ = 32 >> lsb;
-  c.b0 = blockIdx.y * c.SB;
-  c.nsteps = (int)((c.e1 - c.e0 + c.NJ - 1) / c.NJ);
+  const int b0 = blockIdx.y * SB, nlive = min(SB, B - b0);
+  const bool vec = SB % 4 == 0 && nlive == SB && B % 4 == 0;
+  const int64_t e0 = m2l_off[T], nsrc = m2l_off[T + 1] - e0;
+  const int nsteps = (int)((nsrc + KS - 1) / KS);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t bufsz = buf_floats<SB>(nc);
+  int* deg = (int*)(sm + 2 * bufsz);  // degree of every n
+  for (int n = tid; n < nc; n += blockDim.x) {
+    int a, b, z;
+    mi_decode(n, a, b, z);
+    deg[n] = a + b + z;
+  }
+  // this thread's row and table positions
+  const bool has = tid < nitems;
+  const uint32_t it = has ? items[tid] : 0u;
+  const int m = (int)(it & 0xFFFFu), c = (int)(it >> 16);
+  int ma, mb, mz;
+  mi_decode(m, ma, mb, mz);
+  const int nmax = has && ma + mb + mz < p ? ncoef_of(p - ma - mb - mz) : 0;
+  int idx[CH];
+  bool ok[CH];
+#pragma unroll
+  for (int j = 0; j < CH; j++) {
+    const int n = c * CH + j;
+    ok[j] = n >= 1 && n < nmax;
+    int na = 0, nb = 0, nz = 0;
+    if (ok[j]) mi_decode(n, na, nb, nz);
+    idx[j] = ok[j] ? mi_index(ma + na, mb + nb, mz + nz) : 0;
+  }
+  float acc[SB];
+#pragma unroll
+  for (int b = 0; b < SB; b++) acc[b] = 0.f;
+  // staging: warp w < KS owns source slot w of every step
+  auto meta = [&](int s, int k, int32_t& S, int32_t& od) {
+    const int64_t e = (int64_t)s * KS + k;
+    const bool v = s < nsteps && e < nsrc;
+    S = v ? m2l_src[e0 + e] : -1;
+    od = v ? m2l_opdl[e0 + e] : 0;
+  };
+  auto stage = [&](float* buf, int k, int32_t S, int32_t od) {
+    float* brow = buf + (size_t)k * nc;
+    float* qblk = buf + (size_t)KS * nc + (size_t)k * nc * SB;
+    if (S < 0) {
+      for (int i = lane; i < nc; i += 32) brow[i] = 0.f;
+      for (int i = lane; i < nc * SB; i += 32) qblk[i] = 0.f;
+      if (lane == 0) buf[(size_t)KS * nc * (1 + SB) + k] = 0.f;
+      return;
+    }
+    const float* trow = tab + (int64_t)(od & 0xFFFFFF) * nc;
+    for (int i = lane; i < nc; i += 32) cp_async4(brow + i, trow + i);
+    const float* q = Q + (int64_t)S * nc * B + b0;
+    bool done = false;
+    if constexpr (SB % 4 == 0) {
+      if (vec) {
+        for (int i = lane; i < nc * (SB / 4); i += 32) {
+          const int n = i / (SB / 4), v4 = i % (SB / 4);
+          cp_async16(qblk + n * SB + 4 * v4, q + (int64_t)n * B + 4 * v4);
+        }
+        done = true;
+      }
+    }
+    if (!done)
+      for (int i = lane; i < nc * SB; i += 32) {
+        const int n = i / SB, b = i % SB;
+        if (b < nlive)
+          cp_async4(qblk + i, q + (int64_t)n * B + b);
+        else
+          qblk[i] = 0.f;
+      }
+    if (lane == 0) buf[(size_t)KS * nc * (1 + SB) + k] = (float)(od >> 24);  // level difference
+  };
+  int32_t S0 = -1, od0 = 0, S1 = -1, od1 = 0;
+  const int kw = warp < KS ? warp : -1;
+  if (kw >= 0) {
+    meta(0, kw, S0, od0);
+    meta(1, kw, S1, od1);
+  }
+  __syncthreads();  // degrees
+  if (kw >= 0) stage(sm, kw, S0, od0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int s = 0; s < nsteps; s++) {
+    float* buf = sm + (size_t)(s & 1) * bufsz;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();  // step s staged; step s - 1 consumed
+    // f_S^|n| = 2^(dl |n|) on the staged moments of sources on another level
+    const float* dls = buf + (size_t)KS * nc * (1 + SB);
+    for (int k = 0; k < KS; k++) {
+      const int dl = (int)dls[k];
+      if (dl == 0) continue;
+      float* qblk = buf + (size_t)KS * nc + (size_t)k * nc * SB;
+      for (int i = tid; i < nc * SB; i += blockDim.x) qblk[i] = ldexpf(qblk[i], dl * deg[i / SB]);
+    }
+    int32_t S2 = -1, od2 = 0;
+    if (kw >= 0) {
+      if (s + 1 < nsteps) stage(sm + (size_t)((s + 1) & 1) * bufsz, kw, S1, od1);
+      meta(s + 2, kw, S2, od2);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    __syncthreads();  // scaled moments visible
+    if (has) {
+#pragma unroll 1
+      for (int k = 0; k < KS; k++) {
+        const float* bs = buf + (size_t)k * nc;
+        const float* qs = buf + (size_t)KS * nc + (size_t)k * nc * SB + (size_t)c * CH * SB;
+#pragma unroll
+        for (int j = 0; j < CH; j++) {
+          if (!ok[j]) continue;
+          const float bv = bs[idx[j]];
+          if constexpr (SB % 4 == 0) {
+#pragma unroll
+            for (int v4 = 0; v4 < SB / 4; v4++) {
+              const float4 q4 = *(const float4*)(qs + j * SB + 4 * v4);
+              acc[4 * v4] = fmaf(bv, q4.x, acc[4 * v4]);
+              acc[4 * v4 + 1] = fmaf(bv, q4.y, acc[4 * v4 + 1]);
+              acc[4 * v4 + 2] = fmaf(bv, q4.z, acc[4 * v4 + 2]);
+              acc[4 * v4 + 3] = fmaf(bv, q4.w, acc[4 * v4 + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int b = 0; b < SB; b++) acc[b] = fmaf(bv, qs[j * SB + b], acc[b]);
+          }
+        }
+      }
+    }
+    S1 = S2;
+    od1 = od2;
+  }
+  // add the chunks of each row in chunk order: partial sums staged in shared memory
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  float* part = sm;  // nitems x SB
+  if (has)
+#pragma unroll
+    for (int b = 0; b < SB; b++) part[tid * SB + b] = acc[b];
+  __syncthreads();
   const float inv = (float)(1.0 / (4.0 * M_PI * ldexp(side, -level[T])));
-  const int warp = threadIdx.x >> 5;
-  if (warp == 0) role_run<P, NR, 0>(c, sm, L, T, inv);
-  if constexpr (NR > 1) if (warp == 1) role_run<P, NR, 1>(c, sm, L, T, inv);
-  if constexpr (NR > 2) if (warp == 2) role_run<P, NR, 2>(c, sm, L, T, inv);
-  if constexpr (NR > 3) if (warp == 3) role_run<P, NR, 3>(c, sm, L, T, inv);
+  // the items of row mm, in chunk order: rowitem[rowoff[mm] .. rowoff[mm + 1])
+  const uint32_t* rowoff = items + nitems;
+  const uint32_t* rowitem = rowoff + nc + 1;
+  for (int q = tid; q < nc * SB; q += blockDim.x) {
+    const int mm = q / SB, b = q % SB;
+    if (b >= nlive) continue;
+    float v = 0.f;
+    for (uint32_t i = rowoff[mm]; i < rowoff[mm + 1]; i++) v += part[rowitem[i] * SB + b];
+    int a2, b2, z2;
+    mi_decode(mm, a2, b2, z2);
+    L[((int64_t)T * nc + mm) * B + b0 + b] = ((a2 + b2 + z2) & 1) ? -inv * v : inv * v;
+  }
+}
+
+template <int CH, int SB>
+void launch_rc(Plan& P, int B, const float* Q, float* L, cudaStream_t s) {
+  const int nthreads = std::max(32 * KS, (P.m2l_rc_nitems + 31) / 32 * 32);  // every source slot has a warp
+  const size_t smem = std::max(sizeof(float) * 2 * buf_floats<SB>(P.nc) + sizeof(int) * P.nc,
+                               sizeof(float) * (size_t)nthreads * SB);
+  static size_t attr = 0;
+  if (smem > attr) {
+    DM_CUDA(cudaFuncSetAttribute(k_m2l32_rc<CH, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((B + SB - 1) / SB));
+  k_m2l32_rc<CH, SB><<<grid, nthreads, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.m2l_tab_opdl, P.m2l_tab,
+                                                  P.m2l_rc_items, P.m2l_rc_nitems, P.cell_level, P.side, P.p, P.nc, B,
+                                                  Q, L);
+  DM_LAUNCH("k_m2l32_rc");
+}
+
+template <int CH>
+void launch_rc_ch(Plan& P, int B, const float* Q, float* L, cudaStream_t s) {
+  if (B == 1)
+    launch_rc<CH, 1>(P, B, Q, L, s);
+  else if (B == 2)
+    launch_rc<CH, 2>(P, B, Q, L, s);
+  else if (B <= 4)
+    launch_rc<CH, 4>(P, B, Q, L, s);
+  else
+    launch_rc<CH, 8>(P, B, Q, L, s);
 }
 
 // b_k(v) for one key per block, FP64 recurrence, rounded to FP32
@@ -462,7 +428,7 @@ __global__ void __launch_bounds__(128) k_m2l_tab_ops(const int4* __restrict__ ke
   __syncthreads();
   // b_k = (-1)^|k| d^k (1/|x|) at v:  |k| r^2 b_k = (2|k|-1) sum k_i v_i b_{k-e_i} - (|k|-1) sum k_i (k_i-1) b_{k-2e_i}
   for (int t = 1; t <= p; t++) {
-    for (int k = tri(t) + threadIdx.x; k < tri(t + 1); k += blockDim.x) {
+    for (int k = ncoef_of(t - 1) + threadIdx.x; k < ncoef_of(t); k += blockDim.x) {
       int ka, kb, kz;
       mi_decode(k, ka, kb, kz);
       double s1 = 0.0, s2 = 0.0;
@@ -479,43 +445,44 @@ __global__ void __launch_bounds__(128) k_m2l_tab_ops(const int4* __restrict__ ke
   for (int k = threadIdx.x; k < nc; k += blockDim.x) tab[(int64_t)blockIdx.x * nc + k] = (float)b[k];
 }
 
-constexpr bool tab_order(int p) { return p == 4 || p == 6 || p == 8; }
-constexpr int tab_warps(int) { return 4; }
 
-template <int P>
-size_t tab_smem(int lsb) {
-  constexpr int NC = tri(P + 1), RS = NC | 1;
-  return sizeof(float) * 2 * (size_t)((32 >> lsb) * RS + 32 * NC);
-}
-
-template <int P>
-void launch_tab(Plan& P_, int B, const float* Q, float* L, cudaStream_t s) {
-  constexpr int NR = tab_warps(P);
-  int lsb = 0;
-  while ((1 << lsb) < B && lsb < 5) lsb++;
-  const size_t smem = tab_smem<P>(lsb);
-  static size_t attr = 0;
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l32_tab<P, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem<P>(0)));
-    attr = tab_smem<P>(0);
-  }
-  const dim3 grid((unsigned)P_.h_m2l_targets.size(), (unsigned)((B + (1 << lsb) - 1) >> lsb));
-  k_m2l32_tab<P, NR><<<grid, 32 * NR, smem, s>>>(P_.m2l_targets, P_.m2l_off, P_.m2l_src, P_.m2l_tab_opdl, P_.m2l_tab,
-                                                 P_.cell_level, P_.side, B, lsb, Q, L);
-  DM_LAUNCH("k_m2l32_tab");
-}
-
-}  // namespace tab
+}  // namespace rc
 
 void build_m2l_tab(Plan& P, const M2lKeys& K) {
-  if (!K.ok || !tab::tab_order(P.p) || K.keys.empty() || K.keys.size() >= (1u << 24)) return;
+  if (!K.ok || K.keys.empty() || K.keys.size() >= (1u << 24)) return;
+  if (P.p > 10) return;  // two staging buffers of 8 sources x 8 states exceed shared memory
   std::vector<int32_t> opdl(K.op.size());
   for (size_t e = 0; e < K.op.size(); e++) {
     const int dl = K.keys[K.op[e]].x;
     if (dl < -128 || dl > 127) return;
     opdl[e] = K.op[e] | (int32_t)((uint32_t)(dl & 255) << 24);
   }
+  // work items: the shortest chunk (8, 16, 32) with at most 1024 items, then per row the
+  // list of its items in chunk order (CSR)
+  std::vector<uint32_t> it;
+  int ch = 0;
+  for (int c : {8, 16, 32}) {
+    it = rc::items(P.p, c);
+    if (it.size() <= 1024) {
+      ch = c;
+      break;
+    }
+  }
+  if (!ch) return;
+  const int nit = (int)it.size();
+  std::vector<uint32_t> rows(nit + P.nc + 1 + nit);
+  std::copy(it.begin(), it.end(), rows.begin());
+  std::vector<uint32_t> cntr(P.nc + 1, 0);
+  for (uint32_t v : it) cntr[(v & 0xFFFFu) + 1]++;
+  for (int m = 0; m < P.nc; m++) cntr[m + 1] += cntr[m];
+  std::copy(cntr.begin(), cntr.end(), rows.begin() + nit);
+  std::vector<uint32_t> fill(cntr.begin(), cntr.end() - 1);
+  for (int i = 0; i < nit; i++) rows[nit + P.nc + 1 + fill[it[i] & 0xFFFFu]++] = (uint32_t)i;
   cudaStream_t s = P.stream;
+  P.m2l_rc_items = dalloc<uint32_t>(P, rows.size());
+  P.m2l_rc_nitems = nit;
+  P.m2l_rc_ch = ch;
+  DM_CUDA(cudaMemcpyAsync(P.m2l_rc_items, rows.data(), rows.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
   P.m2l_tab_opdl = dalloc<int32_t>(P, opdl.size());
   DM_CUDA(cudaMemcpyAsync(P.m2l_tab_opdl, opdl.data(), opdl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   P.m2l_tab = dalloc<float>(P, K.keys.size() * (size_t)P.nc);
@@ -526,7 +493,7 @@ void build_m2l_tab(Plan& P, const M2lKeys& K) {
   }
   cudaError_t e = cudaMemcpyAsync(dkeys, K.keys.data(), K.keys.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    tab::k_m2l_tab_ops<<<(unsigned)K.keys.size(), 128, 0, s>>>(dkeys, P.p, P.nc, P.m2l_tab);
+    rc::k_m2l_tab_ops<<<(unsigned)K.keys.size(), 128, 0, s>>>(dkeys, P.p, P.nc, P.m2l_tab);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -535,12 +502,12 @@ void build_m2l_tab(Plan& P, const M2lKeys& K) {
 }
 
 bool launch_m2l32_tab(Plan& P, int B, const float* Q, float* L, cudaStream_t s) {
-  if (P.m2l_tab == nullptr || P.m2l_tab_opdl == nullptr) return false;
+  if (P.m2l_tab == nullptr || P.m2l_tab_opdl == nullptr || P.m2l_rc_items == nullptr) return false;
   if (P.h_m2l_targets.empty()) return true;
-  switch (P.p) {
-    case 4: tab::launch_tab<4>(P, B, Q, L, s); return true;
-    case 6: tab::launch_tab<6>(P, B, Q, L, s); return true;
-    case 8: tab::launch_tab<8>(P, B, Q, L, s); return true;
+  switch (P.m2l_rc_ch) {
+    case 8: rc::launch_rc_ch<8>(P, B, Q, L, s); return true;
+    case 16: rc::launch_rc_ch<16>(P, B, Q, L, s); return true;
+    case 32: rc::launch_rc_ch<32>(P, B, Q, L, s); return true;
     default: return false;
   }
 }
