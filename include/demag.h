@@ -199,6 +199,33 @@ demag_status demag_eval_noalloc(demag_plan plan, const double* M, int batch, dou
 demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double* const* M, const int* batch,
                               double* const* u, double* const* H, void* cuda_stream);
 
+/* Magnetostatic self-energy of B states (the use of H the paper makes next to
+ * the potential, Sec. 4.1-4.2):
+ *   e[b] = -(1/2) sum_i V_i M_{b,i} . H_{b,i},   E = mu0 e,
+ * V_i the lumped volume of node i (sum over its tets of |Omega_t| / 4; the
+ * mass lumping of H).  M and H as returned by / given to demag_eval: DEVICE
+ * pointers, (B, N_n, 3); e: B doubles, DEVICE.  Deterministic (fixed-order
+ * reduction).  Asynchronous on cuda_stream.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL, batch < 1, host pointers). */
+demag_status demag_energy(demag_plan plan, const double* M, const double* H, int batch, double* e,
+                          void* cuda_stream);
+
+/* Landau-Lifshitz-Gilbert stepping of B independent magnetisation states on
+ * the plan's mesh with the demagnetising field as the effective field (plus a
+ * uniform applied field), in reduced units:
+ *   dm/dt = -1/(1 + alpha^2) [ m x h + alpha m x (m x h) ],
+ *   h = H_demag(Ms m) / Ms + h_ext,  t in units of 1/(gamma mu0 Ms).
+ * `steps` classical fourth-order Runge-Kutta steps of size dt; each stage's
+ * field is one demag_eval of all B stage states (batch <= max_batch); m is
+ * renormalised to unit length after each step.
+ *   m      : DEVICE, (B, N_n, 3) unit vectors, advanced in place.
+ *   h_ext  : 3 doubles (HOST) or NULL (zero).
+ * Synchronous (returns when the steps are done).
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL m, batch out of range, Ms <= 0,
+ * alpha < 0, dt <= 0, steps < 0, host m), DEMAG_ERR_OUT_OF_MEMORY, DEMAG_ERR_CUDA. */
+demag_status demag_llg_rk4(demag_plan plan, double* m, int batch, double Ms, double alpha, const double* h_ext,
+                           double dt, int steps, void* cuda_stream);
+
 demag_status demag_plan_destroy(demag_plan plan);
 
 /* Stages of demag_eval, for the per-stage timers. */

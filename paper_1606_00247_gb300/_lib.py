@@ -83,6 +83,10 @@ def load(build_if_missing: bool = True):
         L.demag_eval_noalloc.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_eval_multi.restype = i32
         L.demag_eval_multi.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.demag_energy.restype = i32
+        L.demag_energy.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.demag_llg_rk4.restype = i32
+        L.demag_llg_rk4.argtypes = [vp, vp, i32, d, d, vp, d, i32, vp]
         L.demag_plan_destroy.restype = i32
         L.demag_plan_destroy.argtypes = [vp]
         L.demag_plan_stats.restype = i32
@@ -124,6 +128,14 @@ def demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
 def demag_eval_multi(plans_ptr, n_plans, M_ptrs, batch_ptr, u_ptrs, H_ptrs, stream_ptr):
     """Several plans in one submission; every argument but n_plans is a pointer to an array."""
     return load().demag_eval_multi(plans_ptr, n_plans, M_ptrs, batch_ptr, u_ptrs, H_ptrs, stream_ptr)
+
+
+def demag_energy(plan, M_ptr, H_ptr, batch, e_ptr, stream_ptr):
+    return load().demag_energy(plan, M_ptr, H_ptr, batch, e_ptr, stream_ptr)
+
+
+def demag_llg_rk4(plan, m_ptr, batch, Ms, alpha, h_ext_ptr, dt, steps, stream_ptr):
+    return load().demag_llg_rk4(plan, m_ptr, batch, Ms, alpha, h_ext_ptr, dt, steps, stream_ptr)
 
 
 def demag_plan_destroy(plan):

@@ -4,6 +4,8 @@ PyTorch supplies device memory and streams; every stage runs in libdemag.so.
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import torch
 
@@ -86,6 +88,34 @@ class Plan:
         if squeeze:
             return u[0], (H[0] if with_H else None)
         return u, (H if with_H else None)
+
+    def energy(self, M, H, stream=None):
+        """e[b] = -(1/2) sum_i V_i M_b,i . H_b,i (demag_energy; E = mu0 e), device tensors (B, N_n, 3)."""
+        if M.dim() == 2:
+            M, H = M.unsqueeze(0), H.unsqueeze(0)
+        if M.dtype != torch.float64 or H.dtype != torch.float64 or not M.is_contiguous() or not H.is_contiguous():
+            raise ValueError("M and H must be contiguous float64 device tensors")
+        e = torch.empty(M.shape[0], dtype=torch.float64, device=M.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        L.check(L.demag_energy(self._h, M.data_ptr(), H.data_ptr(), M.shape[0], e.data_ptr(), s.cuda_stream),
+                "demag_energy")
+        return e
+
+    def llg_rk4(self, m, Ms=1.0, alpha=0.0, h_ext=None, dt=0.01, steps=1, stream=None):
+        """Advance the unit states m (B, N_n, 3), in place, by `steps` RK4 steps of the
+        LLG equation with the demagnetising field (demag_llg_rk4, reduced units)."""
+        if m.dtype != torch.float64 or not m.is_contiguous() or not m.is_cuda:
+            raise ValueError("m must be a contiguous float64 device tensor")
+        if m.dim() == 2:
+            m = m.unsqueeze(0)
+        hx = None
+        if h_ext is not None:
+            hx = (C.c_double * 3)(*[float(v) for v in h_ext])
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        L.check(L.demag_llg_rk4(self._h, m.data_ptr(), m.shape[0], float(Ms), float(alpha),
+                                C.cast(hx, C.c_void_p) if hx is not None else None, float(dt), int(steps),
+                                s.cuda_stream), "demag_llg_rk4")
+        return m
 
     def eval_host(self, M: np.ndarray, with_H=True):
         """Same call with host (numpy) buffers: the library copies in and out."""

@@ -381,6 +381,30 @@ demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double
   });
 }
 
+demag_status demag_energy(demag_plan plan, const double* M, const double* H, int batch, double* e,
+                          void* cuda_stream) {
+  return guarded([&] {
+    if (!plan || !M || !H || !e) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
+    if (batch < 1) fail(DEMAG_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!is_device_ptr(M) || !is_device_ptr(H) || !is_device_ptr(e))
+      fail(DEMAG_ERR_INVALID_ARG, "demag_energy takes device pointers");
+    energy(*plan, M, H, batch, e, (cudaStream_t)cuda_stream);
+  });
+}
+
+demag_status demag_llg_rk4(demag_plan plan, double* m, int batch, double Ms, double alpha, const double* h_ext,
+                           double dt, int steps, void* cuda_stream) {
+  return guarded([&] {
+    if (!plan || !m) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
+    if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
+    if (!(Ms > 0) || !(alpha >= 0) || !(dt > 0) || steps < 0 || !std::isfinite(Ms * alpha * dt))
+      fail(DEMAG_ERR_INVALID_ARG, "need Ms > 0, alpha >= 0, dt > 0, steps >= 0 (finite)");
+    if (!is_device_ptr(m)) fail(DEMAG_ERR_INVALID_ARG, "demag_llg_rk4 takes a device pointer");
+    const double zero[3] = {0.0, 0.0, 0.0};
+    llg_rk4(*plan, m, batch, Ms, alpha, h_ext ? h_ext : zero, dt, steps, (cudaStream_t)cuda_stream);
+  });
+}
+
 demag_status demag_plan_destroy(demag_plan plan) {
   if (!plan) return DEMAG_ERR_INVALID_ARG;
   return guarded([&] {

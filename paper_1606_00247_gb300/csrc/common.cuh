@@ -105,6 +105,7 @@ struct Plan {
   double* tet_geo = nullptr;      // nt x TET_GEO
   double* tet_grad = nullptr;     // nt x 12 gradients of the barycentric coords
   double* tet_vol = nullptr;      // nt, |vol|
+  double* node_vol = nullptr;     // nn, lumped nodal volume (original order), on first use
 
   // cells
   int64_t ncells = 0;
@@ -307,6 +308,11 @@ inline int m2l_table_batch(const Plan& P) {
 void eval_multi(Plan* const* plans, int n, const double* const* M, const int* batch, double* const* u,
                 double* const* H, cudaStream_t s);
 void multi_forget_plan(const Plan* P);
+// energy and LLG stepping (llg.cu); device pointers, user layout (B, N_n, 3)
+const double* node_volumes(Plan& P);
+void energy(Plan& P, const double* M, const double* H, int B, double* e, cudaStream_t s);
+void llg_rk4(Plan& P, double* m, int B, double Ms, double alpha, const double* hext, double dt, int steps,
+             cudaStream_t s);
 // tensor-core M2L (m2l_tc.cu): operator table at plan time; bytes of the packed
 // moments for B states (0 when the tensor-core M2L is off); packs Q into QP and
 // runs the M2L (false: not available for this plan, use the CUDA-core M2L)
