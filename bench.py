@@ -321,11 +321,13 @@ def run_ours(args, rank, world, local_rank):
     w = workload(args)
     if w["mesh"] == "multi":
         return run_multi(args, rank, world, local_rank, w)
+    if args.llg_steps:
+        return run_llg(args, rank, local_rank, w)
     nodes, tets = make_mesh(w)
     B = args.batch
     plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
                 near_mode=args.near_mode, max_batch=B, device=dev, autotune=int(args.autotune),
-                m2l_table_batch=args.m2l_table_batch)
+                m2l_table_batch=args.m2l_table_batch, sources=args.sources)
     st0 = plan.stats()
     w["leaf"] = st0["leaf_size"]  # the leaf kept by the leaf-size tuner (autotune bit 1), else the requested one
     w["p"] = st0["p"]  # the order kept by the order tuner (autotune bit 2), else the requested one
@@ -370,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
     # live per-stage timing pass (CUDA events on the eval stream, inside the library)
     prof = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
                 near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=int(args.autotune) & 1,
-                m2l_table_batch=args.m2l_table_batch)
+                m2l_table_batch=args.m2l_table_batch, sources=args.sources)
     for _ in range(2):
         prof.eval(M, u, H)
     prof.reset_timers()
@@ -391,7 +393,7 @@ def run_ours(args, rank, world, local_rank):
     if args.precision != "fp64" and not args.no_fp64_ref:
         nref = min(B, 2)
         p64 = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64",
-                   near_mode=1, max_batch=nref, device=dev)
+                   near_mode=1, max_batch=nref, device=dev, sources=args.sources)
         u64, H64 = p64.eval(M[:nref])
         torch.cuda.synchronize(dev)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -408,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
         # moderate batch already reaches its throughput)
         nb = min(B, 16)
         p64b = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64",
-                    near_mode=1, max_batch=nb, device=dev)
+                    near_mode=1, max_batch=nb, device=dev, sources=args.sources)
         p64b.eval(M[:nb])
         ev0.record(stream)
         for _ in range(2):
@@ -435,6 +437,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "n_tets": st0["n_tets"], "n_nodes": st0["n_nodes"],
                    "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_gpu": B,
                    "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
+                   "sources": args.sources,
                    "parallelism": f"replicas x{world}", "n_cells": st0["n_cells"], "n_m2l": st0["n_m2l"],
                    "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
                    "plan_ms": st0["plan_ms"], "m2l_operators": st0["n_m2l_ops"],
@@ -454,6 +457,42 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = oracle_sample(nodes, tets, w, make_M(nodes.shape[0], 1, tets=tets, w=w)[0],
                                             budget_s=args.cpu_budget)
     return out
+
+
+def run_llg(args, rank, local_rank, w):
+    """LLG stepping of B states (demag_llg_rk4): classical RK4, each stage one
+    batched evaluation of the B stage states; reports steps/s and the
+    evaluations/s inside them."""
+    import torch
+
+    from paper_1606_00247_gb300 import inputs
+    from paper_1606_00247_gb300.api import Plan
+
+    dev = torch.device(f"cuda:{local_rank}")
+    nodes, tets = make_mesh(w)
+    B = args.batch
+    pl = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
+              near_mode=args.near_mode, max_batch=B, device=dev, autotune=int(args.autotune) & 1,
+              m2l_table_batch=args.m2l_table_batch)
+    m = torch.as_tensor(inputs.smoothed_unit_m(tets, nodes.shape[0], batch=B, seed=inputs.MAG_SEED + 9), device=dev)
+    pl.llg_rk4(m, Ms=1.0, alpha=0.1, dt=0.02, steps=max(1, args.warmup))
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    pl.llg_rk4(m, Ms=1.0, alpha=0.1, dt=0.02, steps=args.llg_steps)  # synchronous
+    dt_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    if rank != 0:
+        return None
+    return {"metric": "LLG RK4 steps/s (B states, 4 batched demag evaluations per step)",
+            "value": args.llg_steps / dt_s, "unit": "steps/s", "higher_is_better": True,
+            "ms_per_step": 1e3 * dt_s / args.llg_steps, "evals_per_s": 4 * B * args.llg_steps / dt_s,
+            "steps": args.llg_steps, "warmup": args.warmup, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": data_note(w), "config": {"workload": args.workload, "batch": B, "precision": args.precision,
+                                             "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"],
+                                             "alpha": 0.1, "dt": 0.02},
+            "clocks": clk}
 
 
 def multi_meshes(w):
@@ -662,6 +701,10 @@ def main():
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", default="tets", choices=["tets", "dipoles"],
+                    help="P1 tetrahedra (the method) or point dipoles at the nodes (the comparison model)")
+    ap.add_argument("--llg-steps", type=int, default=0,
+                    help="time this many LLG RK4 steps of --batch states instead of the evaluation benchmark")
     ap.add_argument("--accuracy-sweep", action="store_true",
                     help="print the FMM-vs-direct error table over p and theta instead of timing")
     args = ap.parse_args()

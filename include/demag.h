@@ -112,11 +112,21 @@ typedef struct {
                           states.  0 = default (8), < 0 = never.  The FP32
                           precision always uses the table M2L when there is
                           one.                                              */
+  int sources;         /* DEMAG_SOURCES_TETS (0): P1 magnetisation on the
+                          tetrahedra, exact moments and analytic near field
+                          (the paper's method); DEMAG_SOURCES_DIPOLES (1):
+                          every node a point dipole V_i M_i (V_i its lumped
+                          volume) with the Laplace kernel and the same tree,
+                          lists and translations -- the node-dipole
+                          comparison the paper makes (Sec. 4); needs
+                          near_mode = 1                                    */
 } demag_options;
+
+enum { DEMAG_SOURCES_TETS = 0, DEMAG_SOURCES_DIPOLES = 1 };
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
  * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0,
- * m2l_table_batch=0. */
+ * m2l_table_batch=0, sources=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and

@@ -155,6 +155,45 @@ def direct(nodes, tets, M, targets=None, nthreads=0):
     return u[0] if squeeze else u
 
 
+def lumped_volumes(nodes, tets):
+    """Lumped nodal volumes V_i = sum over the tets t containing node i of |Omega_t| / 4."""
+    vol = np.abs(tet_volumes(nodes, tets))  # tet_volumes is signed by orientation
+    V = np.zeros(np.asarray(nodes).shape[0])
+    np.add.at(V, np.asarray(tets, dtype=np.int64).ravel(), np.repeat(vol / 4.0, 4))
+    return V
+
+
+def dipole_direct(nodes, tets, M, targets=None, points=None, chunk=512):
+    """Point-dipole comparison model (the node-dipole treatment the paper compares
+    with, Sec. 4): every node j carries the dipole V_j M_j and
+        u(r) = 1/(4 pi) sum_j V_j M_j . (r - r_j) / |r - r_j|^3,
+    the self term j = i left out at a node.  Evaluated at the nodes `targets`
+    (all by default) or at the off-mesh `points` (n, 3).  M is (N_n, 3) or
+    (B, N_n, 3); plain O(N^2) numpy."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    M = np.asarray(M, dtype=np.float64)
+    squeeze = M.ndim == 2
+    if squeeze:
+        M = M[None]
+    m = lumped_volumes(nodes, tets)[None, :, None] * M  # (B, N_n, 3) dipole moments
+    if points is not None:
+        R = np.asarray(points, dtype=np.float64)
+        self_idx = None
+    else:
+        idx = np.arange(nodes.shape[0]) if targets is None else np.asarray(targets, dtype=np.int64)
+        R = nodes[idx]
+        self_idx = idx
+    u = np.zeros((M.shape[0], R.shape[0]))
+    for a in range(0, R.shape[0], chunk):
+        d = R[a:a + chunk, None, :] - nodes[None, :, :]  # (n, N_n, 3)
+        r2 = np.einsum("ijk,ijk->ij", d, d)
+        if self_idx is not None:
+            r2[np.arange(d.shape[0]), self_idx[a:a + chunk]] = np.inf
+        w = d / (r2 * np.sqrt(r2))[:, :, None]
+        u[:, a:a + chunk] = np.einsum("ijk,bjk->bi", w, m) / (4.0 * np.pi)
+    return u[0] if squeeze else u
+
+
 def lumped_H(nodes, tets, u):
     nodes, tets, u = _f64(nodes), _i32(tets), _f64(u)
     squeeze = u.ndim == 1

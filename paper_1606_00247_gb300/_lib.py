@@ -30,7 +30,7 @@ class demag_options(C.Structure):
                 ("near_mode", C.c_int), ("max_batch", C.c_int), ("autotune", C.c_int), ("profile", C.c_int),
                 ("m2l_targets_per_cta", C.c_int), ("m2l_kps", C.c_int),
                 ("m2l_promote", C.c_int), ("m2l_promote_rows", C.c_int),
-                ("m2l_table_batch", C.c_int)]
+                ("m2l_table_batch", C.c_int), ("sources", C.c_int)]
 
 
 DEMAG_N_STAGES = 9

@@ -305,6 +305,7 @@ void demag_options_default(demag_options* o) {
   o->m2l_promote = 0;
   o->m2l_promote_rows = 0;
   o->m2l_table_batch = 0;
+  o->sources = DEMAG_SOURCES_TETS;
   o->profile = 0;
 }
 
@@ -333,6 +334,10 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
     if (o.m2l_promote_rows < 0 || o.m2l_promote_rows > 64) fail(DEMAG_ERR_INVALID_ARG, "m2l_promote_rows must be in 0..64");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
+    if (o.sources != DEMAG_SOURCES_TETS && o.sources != DEMAG_SOURCES_DIPOLES)
+      fail(DEMAG_ERR_INVALID_ARG, "sources must be DEMAG_SOURCES_TETS or DEMAG_SOURCES_DIPOLES");
+    if (o.sources == DEMAG_SOURCES_DIPOLES && o.near_mode != 1)
+      fail(DEMAG_ERR_UNSUPPORTED, "point-dipole sources need near_mode = 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X6)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     const auto t0 = std::chrono::steady_clock::now();

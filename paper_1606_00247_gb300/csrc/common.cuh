@@ -106,6 +106,7 @@ struct Plan {
   double* tet_grad = nullptr;     // nt x 12 gradients of the barycentric coords
   double* tet_vol = nullptr;      // nt, |vol|
   double* node_vol = nullptr;     // nn, lumped nodal volume (original order), on first use
+  double* node_vol_s = nullptr;   // nn, lumped nodal volume (sorted order), point-dipole sources
 
   // cells
   int64_t ncells = 0;

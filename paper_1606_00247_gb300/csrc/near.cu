@@ -36,16 +36,67 @@ struct Tmp {
 
 __global__ void k_near_keys(const int32_t* __restrict__ targets, const int4* __restrict__ range,
                             const int64_t* __restrict__ p2p_off, const int32_t* __restrict__ p2p_src,
-                            const int32_t* __restrict__ tets_s, const int64_t* __restrict__ key_off, uint64_t* keys) {
+                            const int32_t* __restrict__ tets_s, const int64_t* __restrict__ key_off, bool dipoles,
+                            uint64_t* keys) {
   const int64_t ti = blockIdx.x;
   const int32_t T = targets[ti];
   int64_t o = key_off[ti];
   for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
     const int4 r = range[p2p_src[e]];
-    const int64_t n = 4ll * (r.y - r.x);
-    for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
-      keys[o + q] = ((uint64_t)ti << 32) | (uint32_t)tets_s[4ll * r.x + q];
-    o += n;
+    if (dipoles) {  // the source leaf's own nodes
+      const int64_t n = r.w - r.z;
+      for (int64_t q = threadIdx.x; q < n; q += blockDim.x) keys[o + q] = ((uint64_t)ti << 32) | (uint32_t)(r.z + q);
+      o += n;
+    } else {  // the vertices of the source leaf's tets
+      const int64_t n = 4ll * (r.y - r.x);
+      for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
+        keys[o + q] = ((uint64_t)ti << 32) | (uint32_t)tets_s[4ll * r.x + q];
+      o += n;
+    }
+  }
+}
+
+// point-dipole near field: W[col j][target i] = V_j (r_i - r_j) / (4 pi |r_i - r_j|^3), 0 for i = j
+// (one block per target leaf; every (i, j) pair is written once)
+__global__ void __launch_bounds__(128) k_near_build_dipole(const int32_t* __restrict__ targets,
+                                                           const int4* __restrict__ range,
+                                                           const int64_t* __restrict__ p2p_off,
+                                                           const int32_t* __restrict__ p2p_src,
+                                                           const double* __restrict__ nodes_s,
+                                                           const double* __restrict__ V,
+                                                           const int64_t* __restrict__ coloff,
+                                                           const int32_t* __restrict__ cols,
+                                                           const int64_t* __restrict__ woff, double* W) {
+  const int64_t ti = blockIdx.x;
+  const int4 rT = range[targets[ti]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
+  double* Wt = W + woff[ti];
+  const double inv4pi = 1.0 / (4.0 * M_PI);
+  for (int64_t e = p2p_off[targets[ti]]; e < p2p_off[targets[ti] + 1]; e++) {
+    const int4 rS = range[p2p_src[e]];
+    const int64_t nS = rS.w - rS.z;
+    for (int64_t q = threadIdx.x; q < nS * nT; q += blockDim.x) {
+      const int32_t j = rS.z + (int32_t)(q / nT);
+      const int i = (int)(q % nT), gi = rT.z + i;
+      if (gi == j) continue;
+      int64_t lo = 0, hi = ncol;  // column of node j
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cols[c0 + mid] < j)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      const double d0 = nodes_s[3 * gi] - nodes_s[3 * j], d1 = nodes_s[3 * gi + 1] - nodes_s[3 * j + 1],
+                   d2 = nodes_s[3 * gi + 2] - nodes_s[3 * j + 2];
+      const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      const double f = V[j] * inv4pi / (r2 * sqrt(r2));
+      double* dst = Wt + (lo * nT + i) * 3;
+      dst[0] = f * d0;
+      dst[1] = f * d1;
+      dst[2] = f * d2;
+    }
   }
 }
 
@@ -469,7 +520,7 @@ constexpr int64_t NEAR_KEYS_PER_CHUNK = int64_t(1) << 27;
 void build_near_field(Plan& P) {
   cudaStream_t s = P.stream;
   const int64_t nT = (int64_t)P.h_p2p_targets.size();
-  const bool mixed = P.opt.precision != DEMAG_FP64;
+  const bool mixed = P.opt.precision != DEMAG_FP64, dip = P.opt.sources == DEMAG_SOURCES_DIPOLES;
   P.w_coloff = dalloc<int64_t>(P, nT + 1);
   P.w_off = dalloc<int64_t>(P, nT + 1);
   if (nT == 0) {
@@ -491,7 +542,7 @@ void build_near_field(Plan& P) {
     int64_t n = 0;
     for (int64_t e = P.h_p2p_off[T]; e < P.h_p2p_off[T + 1]; e++) {
       int4 r = P.h_range[P.h_p2p_src[e]];
-      n += 4ll * (r.y - r.x);
+      n += dip ? (int64_t)(r.w - r.z) : 4ll * (r.y - r.x);
     }
     if (n > NEAR_KEYS_PER_CHUNK) fail(DEMAG_ERR_UNSUPPORTED, "near field of one target leaf too large");
     koff[ti + 1] = koff[ti] + n;
@@ -516,7 +567,7 @@ void build_near_field(Plan& P) {
     for (int64_t t = t0; t <= t1; t++) rel[t - t0] = koff[t] - koff[t0];
     DM_CUDA(cudaMemcpyAsync(dkoff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     k_near_keys<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
-                                                     P.tets_s, dkoff.p, keys.p);
+                                                     P.tets_s, dkoff.p, dip, keys.p);
     DM_LAUNCH("k_near_keys");
     size_t t = tb;
     DM_CUDA(cub::DeviceRadixSort::SortKeys(temp.p, t, keys.p, keys_s.p, (int)nk, 0, 64, s));
@@ -581,10 +632,17 @@ void build_near_field(Plan& P) {
       woff = doff.p;
     }
     DM_CUDA(cudaMemsetAsync(W + (mixed ? 0 : hw[t0]), 0, std::max<int64_t>(hw[t1] - hw[t0], 1) * sizeof(double), s));
-    k_near_build<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
-                                                     P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad, P.w_coloff + t0,
-                                                     P.w_cols, woff, W);
-    DM_LAUNCH("k_near_build");
+    if (dip) {
+      k_near_build_dipole<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off,
+                                                              P.p2p_src, P.nodes_s, P.node_vol_s, P.w_coloff + t0,
+                                                              P.w_cols, woff, W);
+      DM_LAUNCH("k_near_build_dipole");
+    } else {
+      k_near_build<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
+                                                       P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad, P.w_coloff + t0,
+                                                       P.w_cols, woff, W);
+      DM_LAUNCH("k_near_build");
+    }
     if (mixed) {
       // FP32 copy, [col][node][4] per target leaf (16-byte entries)
       k_pack_w32<<<(unsigned)(t1 - t0), 256, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.w_coloff + t0, woff,

@@ -324,6 +324,7 @@ struct TravCells {
   const double* rsrc;
   const double* rtgt;
   double theta;
+  int dipoles;  // sources are the cells' nodes (point dipoles), not their tets
 };
 
 __device__ __forceinline__ void push(uint64_t* buf, unsigned long long* cnt, unsigned long long cap, int32_t a,
@@ -336,7 +337,7 @@ __device__ void interact(const TravCells& C, int32_t A, int32_t B, uint64_t* m2l
                          unsigned long long* cnt, unsigned long long cap_m2l, unsigned long long cap_p2p,
                          unsigned long long cap_nxt) {
   int4 ra = C.range[A], rb = C.range[B];
-  if (ra.w == ra.z || rb.y == rb.x) return;
+  if (ra.w == ra.z || (C.dipoles ? rb.w == rb.z : rb.y == rb.x)) return;  // no targets / no sources
   double d = dist_rn(C.centre[3 * A], C.centre[3 * A + 1], C.centre[3 * A + 2], C.centre[3 * B], C.centre[3 * B + 1],
                      C.centre[3 * B + 2]);
   if (__dadd_rn(C.rtgt[A], C.rsrc[B]) < __dmul_rn(C.theta, d))
@@ -430,6 +431,40 @@ __global__ void k_tet_cols(const int4* __restrict__ range, const int32_t* __rest
     }
     tet_col[4ll * r.x + q] = (int32_t)(b - b0);
   }
+}
+
+// point-dipole sources: lumped nodal volume V_i = sum_{t ni i} |Omega_t| / 4 (sorted order)
+__global__ void k_node_vol_sorted(int64_t nn, const int64_t* __restrict__ nt_off, const int32_t* __restrict__ nt_tet,
+                                  const double* __restrict__ vol, double* V) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  double v = 0.0;
+  for (int64_t e = nt_off[i]; e < nt_off[i + 1]; e++) v += vol[nt_tet[e]];
+  V[i] = 0.25 * v;
+}
+
+// point-dipole moment operator: Ghat[e][m] = V_i y^m / m!, y = r_i - c (one block per source
+// leaf, one thread per multi-index m, |m| <= p - 1)
+__global__ void k_ghat_dipole(const int32_t* __restrict__ leaves, int64_t nleaves, const double* __restrict__ centre,
+                              const double* __restrict__ nodes_s, const double* __restrict__ V,
+                              const int64_t* __restrict__ sup_off, const int32_t* __restrict__ sup_node, int pm1,
+                              int nc1, double* Ghat) {
+  const int64_t li = blockIdx.x;
+  if (li >= nleaves || threadIdx.x >= nc1) return;
+  const int32_t c = leaves[li];
+  int ma, mb, mc;
+  mi_decode(threadIdx.x, ma, mb, mc);
+  for (int64_t e = sup_off[c]; e < sup_off[c + 1]; e++) {
+    const int32_t i = sup_node[e];
+    const double y0 = nodes_s[3 * i] - centre[3 * c], y1 = nodes_s[3 * i + 1] - centre[3 * c + 1],
+                 y2 = nodes_s[3 * i + 2] - centre[3 * c + 2];
+    double g = V[i];
+    for (int k = 1; k <= ma; k++) g *= y0 / k;
+    for (int k = 1; k <= mb; k++) g *= y1 / k;
+    for (int k = 1; k <= mc; k++) g *= y2 / k;
+    Ghat[e * nc1 + threadIdx.x] = g;
+  }
+  (void)pm1;
 }
 
 // Exact moment operator of a source leaf (Sec. 2.2, Eq. expCoeffs): for every
@@ -729,11 +764,14 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   DM_LAUNCH("k_centres");
   k_radii<<<(int)nc, 256, 0, s>>>(P.cell_range, P.cell_centre, P.nodes_s, P.tets_s, P.cell_rsrc, P.cell_rtgt);
   DM_LAUNCH("k_radii");
+  const bool dip = P.opt.sources == DEMAG_SOURCES_DIPOLES;
+  if (dip)  // point dipoles at the cell's own nodes: the source radius is the node radius
+    DM_CUDA(cudaMemcpyAsync(P.cell_rsrc, P.cell_rtgt, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
 
   // dual tree traversal (Sec. 3.3, Listings 1-2), breadth first
   {
     TravCells C{P.cell_range, P.cell_level, P.cell_child0, P.cell_nchild,
-                P.cell_centre, P.cell_rsrc, P.cell_rtgt, P.opt.theta};
+                P.cell_centre, P.cell_rsrc, P.cell_rtgt, P.opt.theta, dip ? 1 : 0};
     size_t cap_m = std::max<int64_t>(1024, 64 * nc), cap_p = std::max<int64_t>(1024, 32 * nc),
            cap_f = std::max<int64_t>(1024, 16 * nc);
     Tmp<uint64_t> m2l(cap_m), p2p(cap_p), cur(cap_f), nxt(cap_f);
@@ -832,11 +870,12 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
       int64_t ntg = h_range[c].w - h_range[c].z, nsrc = 0;
       for (int64_t e = h_p2p_off[c]; e < h_p2p_off[c + 1]; e++) {
         int4 r = h_range[h_p2p_src[e]];
-        nsrc += r.y - r.x;
+        nsrc += dip ? r.w - r.z : r.y - r.x;
       }
       P.n_p2p_pairs += ntg * nsrc;
     }
-    if (leaf && h_range[c].y > h_range[c].x) P.h_src_leaves.push_back((int32_t)c);
+    if (leaf && (dip ? h_range[c].w > h_range[c].z : h_range[c].y > h_range[c].x))
+      P.h_src_leaves.push_back((int32_t)c);
   }
 
   P.m2l_targets = dalloc<int32_t>(P, std::max<size_t>(P.h_m2l_targets.size(), 1));
@@ -857,7 +896,23 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   DM_CUDA(cudaMemcpyAsync(P.src_leaves, P.h_src_leaves.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   P.sup_off = dalloc<int64_t>(P, nc + 1);
   P.tet_col = dalloc<int32_t>(P, 4 * nt);
-  {
+  if (dip) {  // a dipole leaf's support is its own nodes (sorted ids r.z .. r.w - 1)
+    std::vector<int64_t> so(nc + 1, 0);
+    std::vector<int32_t> sn;
+    std::vector<char> is_src(nc, 0);
+    for (int32_t c : P.h_src_leaves) is_src[c] = 1;
+    for (int64_t c = 0; c < nc; c++) {
+      if (is_src[c])
+        for (int32_t i = h_range[c].z; i < h_range[c].w; i++) sn.push_back(i);
+      so[c + 1] = (int64_t)sn.size();
+    }
+    P.n_sup = (int64_t)sn.size();
+    P.sup_node = dalloc<int32_t>(P, std::max<int64_t>(P.n_sup, 1));
+    DM_CUDA(cudaMemcpyAsync(P.sup_off, so.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (P.n_sup)
+      DM_CUDA(cudaMemcpyAsync(P.sup_node, sn.data(), sn.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  } else {
     std::vector<int64_t> koff(nsl + 1, 0);
     for (int64_t i = 0; i < nsl; i++) {
       int4 r = h_range[P.h_src_leaves[i]];
@@ -891,8 +946,8 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     DM_LAUNCH("k_tet_cols");
   }
 
-  // exact-moment operators of the source leaves (Sec. 2.2)
-  {
+  // exact-moment operators of the source leaves (Sec. 2.2); dipoles after the node volumes below
+  if (!dip) {
     int pm1 = P.p - 1;
     P.nc1 = ncoef_of(pm1);
     int sgm = (P.p - 1 + 1) / 2;  // degree 2s+1 >= p
@@ -931,6 +986,22 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     for (int64_t q = 0; q < 4 * nt; q++) off[hk[q] + 1]++;
     for (int64_t i = 0; i < nn; i++) off[i + 1] += off[i];
     DM_CUDA(cudaMemcpyAsync(P.nt_off, off.data(), (nn + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // point dipoles: lumped nodal volumes (sorted order), then the moment operator
+  // Ghat[e][m] = V_i y_i^m / m! at the support node i = sup_node[e], y_i = r_i - c_leaf
+  if (dip) {
+    P.node_vol_s = dalloc<double>(P, nn);
+    k_node_vol_sorted<<<nblk(nn, 256), 256, 0, s>>>(nn, P.nt_off, P.nt_tet, P.tet_vol, P.node_vol_s);
+    DM_LAUNCH("k_node_vol_sorted");
+    P.nc1 = ncoef_of(P.p - 1);
+    P.Ghat = dalloc<double>(P, std::max<int64_t>(P.n_sup, 1) * P.nc1);
+    const int threads = ((P.nc1 + 31) / 32) * 32;
+    k_ghat_dipole<<<(int)std::max<int64_t>(nsl, 1), threads, 0, s>>>(P.src_leaves, nsl, P.cell_centre, P.nodes_s,
+                                                                      P.node_vol_s, P.sup_off, P.sup_node, P.p - 1,
+                                                                      P.nc1, P.Ghat);
+    DM_LAUNCH("k_ghat_dipole");
     DM_CUDA(cudaStreamSynchronize(s));
   }
 
