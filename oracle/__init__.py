@@ -14,7 +14,9 @@ The C sources (``oracle_direct.c``, ``oracle_fmm.c``) implement, from the paper
   * exact tet moments (Eq. expCoeffs), M2M / M2L / L2L / L2P (Sec. 2, 2.3),
   * the octree, radii, MAC and dual tree traversal (Sec. 3.1-3.3),
   * the plain CPU FMM.
-This module is only ctypes marshalling around them.
+This module is ctypes marshalling around them, plus two plain numpy routines:
+the lumped nodal volumes and the direct sum of the point-dipole comparison
+model (dipole_direct).
 """
 from __future__ import annotations
 
