@@ -27,16 +27,6 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t > 0 ? (n
 
 namespace {
 
-__device__ __forceinline__ void load_mi(int nc, unsigned char (*mi)[3]) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    int a, b, c;
-    mi_decode(i, a, b, c);
-    mi[i][0] = (unsigned char)a;
-    mi[i][1] = (unsigned char)b;
-    mi[i][2] = (unsigned char)c;
-  }
-}
-
 __global__ void k_gather_M32(int64_t nn, int B, const int32_t* __restrict__ perm, const double* __restrict__ M,
                              float* Ms, double* Ms64) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -162,77 +152,6 @@ __global__ void k_m2m32(const int32_t* __restrict__ parents, int64_t npar, const
     }
   }
   Q[P * per + (int64_t)n * B + b] = acc;
-}
-
-// CUDA-core M2L: one block per target cell, threads over (m, state)
-__global__ void k_m2l32(const int32_t* __restrict__ targets, const int64_t* __restrict__ m2l_off,
-                        const int32_t* __restrict__ m2l_src, const double* __restrict__ centre,
-                        const int32_t* __restrict__ level, double side, int p, int nc, int B,
-                        const float* __restrict__ Q, float* L) {
-  __shared__ unsigned char mi[MAX_NCOEF][3];
-  __shared__ float bk[MAX_NCOEF];
-  __shared__ float fp[MAX_P + 1];
-  load_mi(nc, mi);
-  const int32_t T = targets[blockIdx.x];
-  const double sT = ldexp(side, -level[T]);
-  const double cx = centre[3 * T], cy = centre[3 * T + 1], cz = centre[3 * T + 2];
-  // this block handles the (m, state) items [i0, i1): at most PER per thread
-  constexpr int PER = 8;
-  const int i0 = blockIdx.y * blockDim.x * PER, i1 = min(nc * B, i0 + (int)blockDim.x * PER);
-  float acc[PER];
-  for (int r = 0; r < PER; r++) acc[r] = 0;
-  for (int64_t e = m2l_off[T]; e < m2l_off[T + 1]; e++) {
-    const int32_t S = m2l_src[e];
-    const float x = (float)((cx - centre[3 * S]) / sT), y = (float)((cy - centre[3 * S + 1]) / sT),
-                z = (float)((cz - centre[3 * S + 2]) / sT);
-    const float r2 = x * x + y * y + z * z;
-    const int dl = level[T] - level[S];  // s_S / s_T = 2^dl
-    __syncthreads();
-    if (threadIdx.x == 0) bk[0] = rsqrtf(r2);
-    if (threadIdx.x <= p) fp[threadIdx.x] = ldexpf(1.f, dl * (int)threadIdx.x);
-    __syncthreads();
-    for (int t = 1; t <= p; t++) {
-      const int o = t * (t + 1) * (t + 2) / 6, cnt = (t + 1) * (t + 2) / 2;
-      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int k = o + q;
-        const int ka = mi[k][0], kb = mi[k][1], kz = mi[k][2];
-        float s1 = 0, s2 = 0;
-        if (ka) s1 += ka * x * bk[mi_index(ka - 1, kb, kz)];
-        if (kb) s1 += kb * y * bk[mi_index(ka, kb - 1, kz)];
-        if (kz) s1 += kz * z * bk[mi_index(ka, kb, kz - 1)];
-        if (ka > 1) s2 += ka * (ka - 1) * bk[mi_index(ka - 2, kb, kz)];
-        if (kb > 1) s2 += kb * (kb - 1) * bk[mi_index(ka, kb - 2, kz)];
-        if (kz > 1) s2 += kz * (kz - 1) * bk[mi_index(ka, kb, kz - 2)];
-        bk[k] = ((2 * t - 1) * s1 - (t - 1) * s2) / (t * r2);
-      }
-      __syncthreads();
-    }
-    const float* Qs = Q + (int64_t)S * nc * B;
-    int r = 0;
-    for (int idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x, r++) {
-      const int m = idx / B, b = idx - m * B;
-      const int ma = mi[m][0], mb = mi[m][1], mz = mi[m][2];
-      const int tm = ma + mb + mz;
-      float a = 0;
-      int n = 0;
-      for (int t = 0; t <= p - tm; t++) {
-        float at = 0;
-        for (int j = 0; j <= t; j++)
-          for (int cz2 = 0; cz2 <= j; cz2++, n++)
-            at += bk[mi_index(t - j + ma, j - cz2 + mb, cz2 + mz)] * Qs[(int64_t)n * B + b];
-        a += fp[t] * at;
-      }
-      acc[r] += a;
-    }
-  }
-  int r = 0;
-  const float inv = (float)(1.0 / (4.0 * M_PI * sT));
-  for (int idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x, r++) {
-    const int m = idx / B, b = idx - m * B;
-    const int tm = mi[m][0] + mi[m][1] + mi[m][2];
-    const float sg = (tm & 1) ? -inv : inv;
-    L[((int64_t)T * nc + m) * B + b] = sg * acc[r];
-  }
 }
 
 // L2L from the parents of one level: thread per (parent, m, state) feeding all
@@ -519,7 +438,7 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   double *ud, *Hd;
   const bool dev = eval_io_begin(P, W, M, B, u, H, &Md, &ud, &Hd, s);
   const bool otf = P.opt.near_mode == 0;
-  const int p = P.p, nc = P.nc;
+  const int nc = P.nc;
   StageClock clk(P, s, profile_ok);
   clk.begin(DEMAG_STAGE_GATHER);
   k_gather_M32<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms32, otf ? W.Ms : nullptr);
@@ -555,13 +474,8 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
     clk.launched(2);
   } else if ((!tc_prec || B <= m2l_table_batch(P)) && launch_m2l32_tab(P, B, W.Q32, W.L32, s)) {
     clk.launched();
-  } else if (launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s)) {
-    clk.launched();
   } else {
-    dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((nc * B + 128 * 8 - 1) / (128 * 8)));
-    k_m2l32<<<grid, 128, 0, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre, P.cell_level, P.side, p, nc, B,
-                                 W.Q32, W.L32);
-    DM_LAUNCH("k_m2l32");
+    launch_m2l32_fast(P, B, W.Q32, W.L32, W.err, s);  // orders without a derivative table
     clk.launched();
   }
   clk.end();
