@@ -1,0 +1,46 @@
+"""Host-side logic of bench.py that needs no GPU: workload overrides, the choice
+of M2L path behind the roofline line, the issued-tile flop model of the
+tensor-core M2L, and the roofline record built from per-stage timers."""
+import os
+import sys
+import types
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_workload_overrides():
+    a = types.SimpleNamespace(workload="sphere200k", p=6, leaf=0, theta=0.0)
+    w = bench.workload(a)
+    assert (w["p"], w["leaf"], w["theta"]) == (6, 128, 0.5)
+    assert bench.WORKLOADS["sphere200k"]["p"] == 8  # the table itself is not modified
+
+
+def test_m2l_path_choice():
+    assert not bench.m2l_on_tensor_cores("bf16x3", 8, 0)  # table M2L up to 8 states by default
+    assert bench.m2l_on_tensor_cores("bf16x3", 9, 0)
+    assert bench.m2l_on_tensor_cores("bf16x3", 4, -1)  # never the table
+    assert not bench.m2l_on_tensor_cores("bf16x3", 32, 32)
+    assert not bench.m2l_on_tensor_cores("fp32", 128, 0)
+
+
+def test_m2l_counts():
+    assert bench.m2l_macs(8) == 3003 and bench.m2l_macs(4) == 210  # C(p + 6, 6)
+    # split BF16, p = 8: k-step row prefixes 176, 64, 48, 32 and seven of 16, K = 16, three MMAs
+    rows = [176, 64, 48, 32] + [16] * 7
+    assert bench.m2l_tile_flops(8, "bf16x3") == 2.0 * sum(r * 16 for r in rows) * 3
+
+
+def test_roofline_record_tensor_and_alu():
+    stats = {"stage_ms": {"m2l": 80.0, "p2p": 30.0}, "stage_launches": {"m2l": 10, "p2p": 10}, "_batch": 128,
+             "p": 8, "n_m2l": 866523, "near_mode": 1, "n_near_cols": 107e6, "leaf_size": 128, "n_tets": 223668,
+             "m2l_targets_per_cta": 1, "m2l_kps": 2}
+    peaks = {"bf16_tflops_sustained": 1744.5, "hbm_gbs": 6689.8}
+    r = bench.roofline_for(stats, 10, "bf16x3", peaks, 2070.0, tensor_m2l=True)
+    assert r["kernel"] == "m2l" and r["bound"] == "tensor" and r["peak"] == 1744.5
+    achieved = 2.0 * 866523 * 3003 * 128 / 8e-3 / 1e12
+    assert abs(r["achieved"] - achieved) < 1e-9 * achieved and abs(r["frac"] - achieved / 1744.5) < 1e-12
+    r2 = bench.roofline_for(stats, 10, "bf16x3", peaks, 2070.0, tensor_m2l=False)
+    assert r2["bound"] == "alu" and abs(r2["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
