@@ -248,7 +248,8 @@ def graded_cube(h0=GRADED_20M_H0, n_incl=50, seed=INCLUSION_SEED):
         for h, r0, r1 in ((h0 / 8, 0.0, r), (h0 / 4, r, r + sa), (h0 / 2, r + sa, r + sa + sb)):
             q = _lattice(c - r1, c + r1, h, rng)
             dq = np.linalg.norm(q - c, axis=1)
-            pts.append(q[(dq >= r0) & (dq < r1)])
+            keep = (dq >= r0) & (dq < r1) & np.all((q > 0.25 * h) & (q < 1.0 - 0.25 * h), axis=1)  # inside the cube
+            pts.append(q[keep])
     pts = np.unique(np.concatenate(pts, 0), axis=0)
     tri = Delaunay(pts)
     tets = tri.simplices.astype(np.int64)
