@@ -67,6 +67,8 @@ def lib():
             L.oracle_tet_potential_gauss3d.argtypes = [vp, vp, vp, i32]
             L.oracle_direct.restype = i32
             L.oracle_direct.argtypes = [vp, i64, vp, i64, vp, i32, vp, i64, vp, i32]
+            L.oracle_direct_charges.restype = i32
+            L.oracle_direct_charges.argtypes = [vp, i64, vp, i64, vp, i64, vp, i32, vp, i64, vp, i32]
             L.oracle_lumped_H.restype = i32
             L.oracle_lumped_H.argtypes = [vp, i64, vp, i64, vp, i32, vp]
             L.oracle_tet_volumes.restype = None
@@ -154,6 +156,38 @@ def direct(nodes, tets, M, targets=None, nthreads=0):
     rc = lib().oracle_direct(_p(nodes), nn, _p(tets), nt, _p(M), B, _p(tg), ntg, _p(u), nthreads)
     if rc:
         raise RuntimeError("oracle_direct failed")
+    return u[0] if squeeze else u
+
+
+def boundary_faces(tets):
+    """(tet, local face) pairs of the faces that belong to one tet only (face f
+    is opposite vertex f)."""
+    t = np.asarray(tets, dtype=np.int64)
+    faces = np.concatenate([np.delete(t, f, axis=1) for f in range(4)])  # (4 N_t, 3), face f of tet j at f N_t + j
+    key = np.sort(faces, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    one = np.where(cnt[inv.ravel()] == 1)[0]
+    return np.stack([one % len(t), one // len(t)], axis=1).astype(np.int32)
+
+
+def direct_charges(nodes, tets, M, targets=None, nthreads=0):
+    """u by the whole-mesh charge route (boundary-face charges + volume charges),
+    the same shape conventions as direct()."""
+    nodes, tets = _f64(nodes), _i32(tets)
+    M = _f64(M)
+    squeeze = M.ndim == 2
+    if squeeze:
+        M = M[None]
+    B = M.shape[0]
+    nn, nt = nodes.shape[0], tets.shape[0]
+    bf = np.ascontiguousarray(boundary_faces(tets))
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    ntg = nn if tg is None else tg.shape[0]
+    u = np.zeros((B, ntg))
+    rc = lib().oracle_direct_charges(_p(nodes), nn, _p(tets), nt, _p(bf), bf.shape[0], _p(M), B, _p(tg), ntg, _p(u),
+                                     nthreads)
+    if rc:
+        raise RuntimeError("oracle_direct_charges failed")
     return u[0] if squeeze else u
 
 

@@ -55,6 +55,12 @@ int oracle_direct(const double* nodes, int64_t n_nodes, const int32_t* tets, int
 int oracle_lumped_H(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                     const double* u, int B, double* H);
 /* Signed volumes (for the mesh-quality checks of the tests). */
+/* The same u by the whole-mesh charge route: boundary-face surface charges
+ * (bfaces: n_bfaces (tet, local face) pairs, face f opposite vertex f) plus the
+ * volume charges of all tets; interior face charges cancel for continuous M. */
+int oracle_direct_charges(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                          const int32_t* bfaces, int64_t n_bfaces, const double* M, int B,
+                          const int64_t* targets, int64_t n_targets, double* u, int nthreads);
 void oracle_tet_volumes(const double* nodes, const int32_t* tets, int64_t n_tets, double* vol);
 
 /* ---- expansions (Sec. 2.2-2.3) -------------------------------------------- */

@@ -454,6 +454,87 @@ int oracle_direct(const double* nodes, int64_t n_nodes, const int32_t* tets, int
   return 0;
 }
 
+/* Whole-mesh charge route: for a continuous P1 magnetisation the surface
+ * charges n.M of an interior face cancel between its two tets (opposite
+ * normals, same M), so the potential is that of the boundary faces' affine
+ * surface charges plus every tet's constant volume charge -div M:
+ *   4 pi u(r) = sum_{boundary (t, f)} int_f n_f.M / R dA + sum_t rho_t int_t 1/R dV.
+ * A route to the same number that never forms an interior face charge.  The
+ * boundary faces are given as (tet, local face) pairs (face f opposite vertex f). */
+int oracle_direct_charges(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                          const int32_t* bfaces, int64_t n_bfaces, const double* M, int B,
+                          const int64_t* targets, int64_t n_targets, double* u, int nthreads) {
+  if (!nodes || !tets || !M || !u || B < 1 || (n_bfaces && !bfaces)) return 1;
+  if (!targets && n_targets != n_nodes) return 1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n_targets; i++) {
+    const int64_t node = targets ? targets[i] : i;
+    const double* r = nodes + 3 * node;
+    for (int b = 0; b < B; b++) {
+      double s = 0;
+      for (int64_t t = 0; t < n_tets; t++) {  /* volume charges */
+        double v[12], Mt[12], Mr[3], J[9];
+        for (int k = 0; k < 4; k++) {
+          const int32_t g = tets[4 * t + k];
+          for (int a = 0; a < 3; a++) {
+            v[3 * k + a] = nodes[3 * (int64_t)g + a];
+            Mt[3 * k + a] = M[((int64_t)b * n_nodes + g) * 3 + a];
+          }
+        }
+        tet_affine T;
+        tet_affine_init(v, &T);
+        tet_field(v, &T, Mt, r, Mr, J);
+        const double rho = -(J[0] + J[4] + J[8]);
+        double vol_int = 0;
+        for (int f = 0; f < 4; f++) {
+          int idx[3];
+          double n[3], I, K[3], h;
+          tet_face(v, f, idx, n);
+          const double* V[3] = {v + 3 * idx[0], v + 3 * idx[1], v + 3 * idx[2]};
+          face_charge_integrals(r, V, n, 1e-14 * T.diam, &I, K, &h);
+          vol_int += -0.5 * h * I;
+        }
+        s += rho * vol_int;
+      }
+      for (int64_t q = 0; q < n_bfaces; q++) {  /* boundary surface charges */
+        const int64_t t = bfaces[2 * q];
+        const int f = bfaces[2 * q + 1];
+        double v[12], Mt[12], Mr[3], J[9];
+        for (int k = 0; k < 4; k++) {
+          const int32_t g = tets[4 * t + k];
+          for (int a = 0; a < 3; a++) {
+            v[3 * k + a] = nodes[3 * (int64_t)g + a];
+            Mt[3 * k + a] = M[((int64_t)b * n_nodes + g) * 3 + a];
+          }
+        }
+        tet_affine T;
+        tet_affine_init(v, &T);
+        tet_field(v, &T, Mt, r, Mr, J);
+        int idx[3];
+        double n[3], I, K[3], h;
+        tet_face(v, f, idx, n);
+        const double* V[3] = {v + 3 * idx[0], v + 3 * idx[1], v + 3 * idx[2]};
+        face_charge_integrals(r, V, n, 1e-14 * T.diam, &I, K, &h);
+        const double Jn[3] = {J[0] * n[0] + J[1] * n[1] + J[2] * n[2], J[3] * n[0] + J[4] * n[1] + J[5] * n[2],
+                              J[6] * n[0] + J[7] * n[1] + J[8] * n[2]};
+        const double sigma0 = dot3(n, Mr) - h * dot3(n, Jn);
+        const double JTn[3] = {J[0] * n[0] + J[3] * n[1] + J[6] * n[2], J[1] * n[0] + J[4] * n[1] + J[7] * n[2],
+                               J[2] * n[0] + J[5] * n[1] + J[8] * n[2]};
+        const double nn = dot3(JTn, n);
+        const double gs[3] = {JTn[0] - nn * n[0], JTn[1] - nn * n[1], JTn[2] - nn * n[2]};
+        s += sigma0 * I + dot3(gs, K);
+      }
+      u[(int64_t)b * n_targets + i] = s / FOUR_PI;
+    }
+  }
+  return 0;
+}
+
 void oracle_tet_volumes(const double* nodes, const int32_t* tets, int64_t n_tets, double* vol) {
   for (int64_t t = 0; t < n_tets; t++) {
     double v[12];

@@ -145,3 +145,21 @@ def test_sphere_uniform_interior_field(orc):
         inner = np.linalg.norm(nodes, axis=1) < 0.5
         errs.append(np.max(np.abs(u[inner] - nodes[inner, 2] / 3.0)))
     assert errs[1] < errs[0] and errs[1] < 0.02
+
+
+def test_whole_mesh_charge_route(orc):
+    """For continuous P1 M the interior face charges cancel, so the boundary-face
+    charges plus the volume charges give the same u as the per-tet sum; the
+    boundary faces found are exactly the cube's surface triangles."""
+    for nodes, tets in (inputs.unit_cube(3), inputs.sphere(h=0.3)):
+        M = inputs.gaussian_unit_m(nodes.shape[0], batch=2, seed=17)
+        a = orc.direct(nodes, tets, M)
+        b = orc.direct_charges(nodes, tets, M)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    nodes, tets = inputs.unit_cube(3)
+    bf = orc.boundary_faces(tets)
+    assert len(bf) == 6 * 2 * 3 * 3  # two triangles per boundary square
+    faces = np.array([[tets[t][k] for k in range(4) if k != f] for t, f in bf])
+    xyz = nodes[faces]  # (n_faces, 3 vertices, 3 coordinates)
+    on_plane = np.any(np.all(np.isclose(xyz, 0.0), axis=1) | np.all(np.isclose(xyz, 1.0), axis=1), axis=1)
+    assert np.all(on_plane)  # every boundary face lies in a face plane of the cube
