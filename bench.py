@@ -281,6 +281,7 @@ def oracle_sample(nodes, tets, w, M1, budget_s=20.0, frac=None):
     ex = tr.export()
     leaves = np.where((ex["cell_child"][:, 1] == 0) & (ex["cell_ranges"][:, 3] > ex["cell_ranges"][:, 2]))[0]
     nthreads = oracle.max_threads()
+    resize = frac is None  # a given fraction (repeated samples) is kept as it is
     t0 = time.perf_counter()
     tr.fmm(M1, w["p"], target_leaves=np.zeros(0, np.int64))
     t_up = time.perf_counter() - t0
@@ -293,12 +294,18 @@ def oracle_sample(nodes, tets, w, M1, budget_s=20.0, frac=None):
         per_leaf = t_probe / len(probe)
         n = int(max(len(probe), min(len(leaves), (budget_s - t_up) / per_leaf)))
         frac = n / len(leaves)
-    n = max(1, int(round(frac * len(leaves))))
-    sample = leaves[np.linspace(0, len(leaves) - 1, n).astype(np.int64)]
-    t0 = time.perf_counter()
-    tr.fmm(M1, w["p"], target_leaves=sample)
-    t_tot = time.perf_counter() - t0
-    t_down = max(0.0, t_tot - t_up)
+    for attempt in range(2):
+        n = max(1, int(round(frac * len(leaves))))
+        sample = leaves[np.linspace(0, len(leaves) - 1, n).astype(np.int64)]
+        t0 = time.perf_counter()
+        tr.fmm(M1, w["p"], target_leaves=sample)
+        t_tot = time.perf_counter() - t0
+        t_down = max(0.0, t_tot - t_up)
+        # a small probe overestimates the per-leaf time (few leaves per thread): when the sample
+        # took under half the budget, size it once more from its own per-leaf time
+        if attempt or not resize or t_up + t_down >= 0.5 * budget_s or n >= len(leaves) or t_down <= 0:
+            break
+        frac = min(1.0, frac * (budget_s - t_up) / t_down)
     t_eval = t_up + t_down * len(leaves) / len(sample)
     return {"value": 1.0 / t_eval, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"plain CPU FMM, p={w['p']}, 1 state: full upward pass ({t_up:.2f} s) + "
