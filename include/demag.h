@@ -261,15 +261,17 @@ typedef struct {
   int64_t n_near_cols;   /* stored (target node, source node) coefficients   */
   int64_t device_bytes;  /* device memory held by the plan                   */
   double lo[3], side, scale; /* bounding cube and Morton scale              */
-  double plan_ms;        /* wall time of demag_plan_create                    */
+  double plan_ms;        /* wall time of demag_plan_create (with the order and
+                            leaf tuning when autotune asks for them)        */
   int p, leaf_size, precision, near_mode, max_batch;
   double theta;
   int64_t eval_launches;           /* kernels launched by the last demag_eval */
   int64_t n_evals_profiled;        /* evals accumulated in stage_ms          */
   double stage_ms[DEMAG_N_STAGES]; /* summed per-stage device time (profile=1) */
   int64_t stage_launches[DEMAG_N_STAGES];
-  int64_t n_m2l_ops;     /* distinct M2L translation operators tabulated for
-                            the tensor-core M2L (0: CUDA-core M2L)          */
+  int64_t n_m2l_ops;     /* distinct M2L translation keys (level difference,
+                            lattice offset) tabulated for the tensor-core and
+                            table-driven M2L of the mixed path (0: none)    */
   int m2l_kps;           /* tensor-core M2L ring: k-steps per slot          */
   int m2l_ring_bytes;    /* tensor-core M2L ring: shared memory per CTA     */
   int m2l_targets_per_cta; /* tensor-core M2L: target cells sharing each
