@@ -92,6 +92,8 @@ def lib():
             L.oracle_multipole_eval.argtypes = [i32, vp, vp, vp]
             L.oracle_tree_build.restype = vp
             L.oracle_tree_build.argtypes = [vp, i64, vp, i64, i32, d, C.POINTER(C.c_int)]
+            L.oracle_tree_build_sources.restype = vp
+            L.oracle_tree_build_sources.argtypes = [vp, i64, vp, i64, i32, d, i32, C.POINTER(C.c_int)]
             L.oracle_tree_free.restype = None
             L.oracle_tree_free.argtypes = [vp]
             L.oracle_tree_info.restype = None
@@ -315,11 +317,13 @@ def multipole_eval(p, c, Q, r):
 class Tree:
     """Octree, radii and interaction lists of Sec. 3.1-3.3 (see oracle_fmm.c)."""
 
-    def __init__(self, nodes, tets, leaf_size=32, theta=0.5):
+    def __init__(self, nodes, tets, leaf_size=32, theta=0.5, sources="tets"):
+        """sources: "tets" (the method) or "dipoles" (point dipoles V_i M_i at the nodes)."""
         self.nodes, self.tets = _f64(nodes), _i32(tets)
         st = C.c_int(0)
-        h = lib().oracle_tree_build(_p(self.nodes), self.nodes.shape[0], _p(self.tets), self.tets.shape[0],
-                                    leaf_size, theta, C.byref(st))
+        h = lib().oracle_tree_build_sources(_p(self.nodes), self.nodes.shape[0], _p(self.tets),
+                                            self.tets.shape[0], leaf_size, theta,
+                                            {"tets": 0, "dipoles": 1}[sources], C.byref(st))
         if not h or st.value:
             raise ValueError("oracle_tree_build rejected the input")
         self._h = h

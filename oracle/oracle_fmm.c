@@ -415,6 +415,8 @@ struct oracle_tree {
   int nlevels;
   int64_t n_m2l, n_p2p;
   int64_t *m2l_off, *m2l_src, *p2p_off, *p2p_src;
+  int dipoles;      /* sources: 0 the tets, 1 point dipoles V_i M_i at the nodes */
+  double* node_vol; /* lumped nodal volumes (dipole sources) */
 };
 
 static uint64_t spread_bits(uint64_t q) {
@@ -495,7 +497,7 @@ static int mac_ok(const oracle_tree* t, int64_t T, int64_t S) {
 
 /* Listing 2 with the MAC tested first. */
 static void interact(const oracle_tree* t, int64_t A, int64_t B, pair_vec* stack, pair_vec* m2l, pair_vec* p2p) {
-  if (t->ne[A] == t->nb[A] || t->te[B] == t->tb[B]) return;
+  if (t->ne[A] == t->nb[A] || (t->dipoles ? t->ne[B] == t->nb[B] : t->te[B] == t->tb[B])) return;
   if (mac_ok(t, A, B))
     pv_push(m2l, A, B);
   else if (is_leaf(t, A) && is_leaf(t, B))
@@ -517,6 +519,11 @@ static void build_csr(pair_vec* v, int64_t ncells, int64_t** off, int64_t** src)
 
 oracle_tree* oracle_tree_build(const double* nodes, int64_t nn, const int32_t* tets, int64_t nt, int leaf,
                                double theta, int* status) {
+  return oracle_tree_build_sources(nodes, nn, tets, nt, leaf, theta, 0, status);
+}
+
+oracle_tree* oracle_tree_build_sources(const double* nodes, int64_t nn, const int32_t* tets, int64_t nt, int leaf,
+                                       double theta, int dipoles, int* status) {
   *status = 1;
   if (!nodes || !tets || nn < 1 || nt < 1 || leaf < 1 || !(theta > 0)) return NULL;
   for (int64_t i = 0; i < 4 * nt; i++)
@@ -526,6 +533,15 @@ oracle_tree* oracle_tree_build(const double* nodes, int64_t nn, const int32_t* t
   t->nt = nt;
   t->leaf = leaf;
   t->theta = theta;
+  t->dipoles = dipoles ? 1 : 0;
+  if (t->dipoles) { /* lumped nodal volumes: a quarter of each incident tet */
+    double* vol = malloc(sizeof(double) * nt);
+    oracle_tet_volumes(nodes, tets, nt, vol);
+    t->node_vol = calloc(nn, sizeof(double));
+    for (int64_t j = 0; j < nt; j++)
+      for (int k = 0; k < 4; k++) t->node_vol[tets[4 * j + k]] += 0.25 * fabs(vol[j]);
+    free(vol);
+  }
   t->nodes_c = malloc(sizeof(double) * 3 * nn);
   memcpy(t->nodes_c, nodes, sizeof(double) * 3 * nn);
   t->tets_c = malloc(sizeof(int32_t) * 4 * nt);
@@ -631,7 +647,7 @@ oracle_tree* oracle_tree_build(const double* nodes, int64_t nn, const int32_t* t
       double d = dist3(nodes + 3 * t->node_perm[i], t->centre + 3 * c);
       if (d > rt) rt = d;
     }
-    t->r_src[c] = rs;
+    t->r_src[c] = t->dipoles ? rt : rs; /* dipoles sit at the cell's own nodes */
     t->r_tgt[c] = rt;
   }
 
@@ -673,6 +689,7 @@ void oracle_tree_free(oracle_tree* t) {
   free(t->parent); free(t->child0); free(t->nchild);
   free(t->centre); free(t->r_src); free(t->r_tgt);
   free(t->m2l_off); free(t->m2l_src); free(t->p2p_off); free(t->p2p_src);
+  free(t->node_vol);
   free(t);
 }
 
@@ -775,10 +792,38 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
     }
   }
 
+  /* P2M of point dipoles: Q_n = sum_i V_i M_i . grad(y^n) at y_i = r_i - c, leaves holding nodes */
+  if (t->dipoles) {
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < ncell; c++) {
+      if (!is_leaf(t, c) || t->ne[c] == t->nb[c]) continue;
+      for (int b = 0; b < B; b++) {
+        double* Qc = Q + ((size_t)b * ncell + c) * nc;
+        for (int64_t i = t->nb[c]; i < t->ne[c]; i++) {
+          const int64_t g = t->node_perm[i];
+          const double* m = M + ((int64_t)b * t->nn + g) * 3;
+          double pw[3][32];
+          for (int a = 0; a < 3; a++) {
+            const double y = t->nodes_c[3 * g + a] - t->centre[3 * c + a];
+            pw[a][0] = 1;
+            for (int e = 1; e <= p; e++) pw[a][e] = pw[a][e - 1] * y;
+          }
+          for (int id = 1; id < nc; id++) {
+            const int nx = T.n[3 * id], ny = T.n[3 * id + 1], nz = T.n[3 * id + 2];
+            double gsum = 0;
+            if (nx) gsum += nx * m[0] * pw[0][nx - 1] * pw[1][ny] * pw[2][nz];
+            if (ny) gsum += ny * m[1] * pw[0][nx] * pw[1][ny - 1] * pw[2][nz];
+            if (nz) gsum += nz * m[2] * pw[0][nx] * pw[1][ny] * pw[2][nz - 1];
+            Qc[id] += t->node_vol[g] * gsum;
+          }
+        }
+      }
+    }
+  }
   /* P2M: leaves holding tets */
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t c = 0; c < ncell; c++) {
-    if (!is_leaf(t, c) || t->te[c] == t->tb[c]) continue;
+    if (t->dipoles || !is_leaf(t, c) || t->te[c] == t->tb[c]) continue;
     double* q = malloc(sizeof(double) * nc);
     for (int b = 0; b < B; b++) {
       double* Qc = Q + ((size_t)b * ncell + c) * nc;
@@ -839,6 +884,18 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
         double un = 0;
         for (int64_t e = t->p2p_off[c]; e < t->p2p_off[c + 1]; e++) {
           int64_t s = t->p2p_src[e];
+          if (t->dipoles) { /* V_j M_j . (r - r_j) / |r - r_j|^3, no self term */
+            for (int64_t jj = t->nb[s]; jj < t->ne[s]; jj++) {
+              const int64_t j = t->node_perm[jj];
+              if (j == node) continue;
+              const double* rj = t->nodes_c + 3 * j;
+              const double* mj = M + ((int64_t)b * t->nn + j) * 3;
+              const double d0 = r[0] - rj[0], d1 = r[1] - rj[1], d2 = r[2] - rj[2];
+              const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+              un += t->node_vol[j] * (mj[0] * d0 + mj[1] * d1 + mj[2] * d2) / (R2 * sqrt(R2));
+            }
+            continue;
+          }
           for (int64_t j = t->tb[s]; j < t->te[s]; j++) {
             double v[12], Mt[12];
             gather_tet(t, t->tet_perm[j], M, b, v, Mt);

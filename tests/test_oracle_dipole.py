@@ -44,3 +44,17 @@ def test_far_potential_is_that_of_the_total_moment(orc):
         ref = d[:, 2] / (4.0 * np.pi * Rr ** 3)  # total moment (0, 0, 1) at the centre
         err = np.abs(u - ref).max() / np.abs(ref).max()
         assert err < 2.0 / Rr, (Rr, err)
+
+
+def test_oracle_dipole_fmm(orc):
+    """The oracle FMM with point-dipole sources (node radii, node moments, point-dipole near
+    field): every pair near (theta -> 0) gives the direct dipole sum; at theta = 0.5 the
+    truncation falls geometrically with p."""
+    nodes, tets = inputs.sphere(h=0.15)
+    M = inputs.gaussian_unit_m(nodes.shape[0], seed=9)
+    ref = orc.dipole_direct(nodes, tets, M)
+    u0 = orc.Tree(nodes, tets, 16, 1e-9, sources="dipoles").fmm(M, 4)
+    assert np.linalg.norm(u0 - ref) / np.linalg.norm(ref) < 1e-12
+    errs = [np.linalg.norm(orc.Tree(nodes, tets, 32, 0.5, sources="dipoles").fmm(M, p) - ref) / np.linalg.norm(ref)
+            for p in (4, 6, 8)]
+    assert errs[0] > 3 * errs[1] > 9 * errs[2] and errs[2] < 1e-3, errs
