@@ -220,11 +220,15 @@ def graded_cube(h0=GRADED_20M_H0, n_incl=50, seed=INCLUSION_SEED):
     rng = np.random.default_rng(seed)
     sa, sb = 0.75 * h0, 1.5 * h0
     cen, rad = [], []
-    while len(cen) < n_incl:
+    for _ in range(1000 * n_incl):
+        if len(cen) == n_incl:
+            break
         c, r = rng.uniform(0.1, 0.9, 3), rng.uniform(0.02, 0.05)
         if all(np.linalg.norm(c - c2) > r + r2 + 2 * (sa + sb) for c2, r2 in zip(cen, rad)):
             cen.append(c)
             rad.append(r)
+    if len(cen) < n_incl:
+        raise ValueError(f"{n_incl} inclusions with their shells do not fit at h0 = {h0}")
     cen, rad = np.array(cen), np.array(rad)
     outer = rad + sa + sb
     pts = []

@@ -29,6 +29,13 @@ def test_graded_cube_small():
     assert inside > 0.25 * (4.0 / 3.0) * np.pi * rad[k] ** 3 * (8.0 / h0) ** 3
 
 
+def test_graded_cube_rejects_inclusions_that_do_not_fit():
+    import pytest
+
+    with pytest.raises(ValueError):
+        inputs.graded_cube(h0=0.25, n_incl=50)
+
+
 def test_batch_meshes_sizes_and_kinds():
     ms = inputs.batch_meshes(n=6, min_tets=2e3, max_tets=2e4)
     sizes = [t.shape[0] for _, t in ms]
