@@ -101,3 +101,30 @@ def test_constant_M_is_face_charge_only(orc):
         dip = vol * np.dot(m0, d) / np.linalg.norm(d) ** 3
         # next term of the multipole series is O(diam/R) relative
         assert abs(a - dip) <= 4.0 / R * abs(dip)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_poisson_equation(orc, seed):
+    """u_t = (1/4 pi) int_t M . grad'(1/R) solves Poisson's equation: its Laplacian is
+    div M inside the tet (-rho, the volume charge) and 0 outside.  The oracle returns
+    4 pi u_t; a 7-point finite-difference Laplacian at interior and exterior points
+    checks it, a relation the integration-by-parts derivation does not use."""
+    rng = np.random.default_rng(100 + seed)
+    v = inputs.random_tet(rng)
+    A, b0 = rng.standard_normal((3, 3)), rng.standard_normal(3)
+    M = np.array([A @ x + b0 for x in v])  # linear M: div M = trace A
+    d = max(np.linalg.norm(v[i] - v[j]) for i in range(4) for j in range(i + 1, 4))
+    h = 2e-3 * d
+    f = lambda r: orc.tet_potential(r, v.ravel(), M.ravel())
+
+    def lap(r):
+        return sum(f(r + h * e) + f(r - h * e) - 2.0 * f(r) for e in np.eye(3)) / h ** 2
+
+    lam = rng.dirichlet(np.ones(4) * 4.0)
+    while lam.min() < 0.1:  # a point well inside: the stencil stays off the faces
+        lam = rng.dirichlet(np.ones(4) * 4.0)
+    inside = lam @ v
+    assert abs(lap(inside) - 4.0 * np.pi * np.trace(A)) < 2e-3 * 4.0 * np.pi * max(1.0, abs(np.trace(A)))
+    outside = v.mean(0) + 2.0 * d * np.array([0.48, 0.6, -0.64])
+    scale = abs(f(outside)) / d ** 2
+    assert abs(lap(outside)) < 1e-4 * scale
