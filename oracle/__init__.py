@@ -318,12 +318,13 @@ class Tree:
     """Octree, radii and interaction lists of Sec. 3.1-3.3 (see oracle_fmm.c)."""
 
     def __init__(self, nodes, tets, leaf_size=32, theta=0.5, sources="tets"):
-        """sources: "tets" (the method) or "dipoles" (point dipoles V_i M_i at the nodes)."""
+        """sources: "tets" (the method), "dipoles" (point dipoles V_i M_i at the nodes) or
+        "patches" (vertex patches lambda_i M_i binned by node, the paper's clustering)."""
         self.nodes, self.tets = _f64(nodes), _i32(tets)
         st = C.c_int(0)
         h = lib().oracle_tree_build_sources(_p(self.nodes), self.nodes.shape[0], _p(self.tets),
                                             self.tets.shape[0], leaf_size, theta,
-                                            {"tets": 0, "dipoles": 1}[sources], C.byref(st))
+                                            {"tets": 0, "dipoles": 1, "patches": 2}[sources], C.byref(st))
         if not h or st.value:
             raise ValueError("oracle_tree_build rejected the input")
         self._h = h

@@ -93,12 +93,14 @@ typedef struct oracle_tree oracle_tree;
 /* status: 0 ok, 1 invalid argument. */
 oracle_tree* oracle_tree_build(const double* nodes, int64_t n_nodes, const int32_t* tets,
                                int64_t n_tets, int leaf_size, double theta, int* status);
-/* The same with the source model chosen: dipoles = 0, the tets (the method);
- * dipoles = 1, point dipoles V_i M_i at the nodes (V_i the lumped volume), with
- * the node radius as source radius, nodes as the source content of a cell,
- * point-dipole moments and the point-dipole near field (self term left out). */
+/* The same with the source model chosen: sources = 0, the tets binned by centroid
+ * (the method); 1, point dipoles V_i M_i at the nodes (V_i the lumped volume),
+ * with the node radius as source radius, point-dipole moments and near field
+ * (self term left out); 2, vertex patches: node i carries lambda_i M_i over the
+ * tets around it (the paper's hat-function clustering), binned by the node,
+ * source radius the farthest vertex of those tets, exact moments and near field. */
 oracle_tree* oracle_tree_build_sources(const double* nodes, int64_t n_nodes, const int32_t* tets,
-                                       int64_t n_tets, int leaf_size, double theta, int dipoles, int* status);
+                                       int64_t n_tets, int leaf_size, double theta, int sources, int* status);
 void oracle_tree_free(oracle_tree* t);
 /* info[0]=n_cells info[1]=n_m2l info[2]=n_p2p info[3]=n_levels info[4]=n_leaves */
 void oracle_tree_info(const oracle_tree* t, int64_t* info);

@@ -415,8 +415,10 @@ struct oracle_tree {
   int nlevels;
   int64_t n_m2l, n_p2p;
   int64_t *m2l_off, *m2l_src, *p2p_off, *p2p_src;
-  int dipoles;      /* sources: 0 the tets, 1 point dipoles V_i M_i at the nodes */
+  int dipoles;      /* sources: point dipoles V_i M_i at the nodes */
+  int patches;      /* sources: vertex patches lambda_i M_i over the tets around node i */
   double* node_vol; /* lumped nodal volumes (dipole sources) */
+  int64_t *nt_off, *nt_tet; /* node -> incident tets (vertex patches) */
 };
 
 static uint64_t spread_bits(uint64_t q) {
@@ -497,7 +499,8 @@ static int mac_ok(const oracle_tree* t, int64_t T, int64_t S) {
 
 /* Listing 2 with the MAC tested first. */
 static void interact(const oracle_tree* t, int64_t A, int64_t B, pair_vec* stack, pair_vec* m2l, pair_vec* p2p) {
-  if (t->ne[A] == t->nb[A] || (t->dipoles ? t->ne[B] == t->nb[B] : t->te[B] == t->tb[B])) return;
+  const int node_sources = t->dipoles || t->patches;
+  if (t->ne[A] == t->nb[A] || (node_sources ? t->ne[B] == t->nb[B] : t->te[B] == t->tb[B])) return;
   if (mac_ok(t, A, B))
     pv_push(m2l, A, B);
   else if (is_leaf(t, A) && is_leaf(t, B))
@@ -523,7 +526,7 @@ oracle_tree* oracle_tree_build(const double* nodes, int64_t nn, const int32_t* t
 }
 
 oracle_tree* oracle_tree_build_sources(const double* nodes, int64_t nn, const int32_t* tets, int64_t nt, int leaf,
-                                       double theta, int dipoles, int* status) {
+                                       double theta, int sources, int* status) {
   *status = 1;
   if (!nodes || !tets || nn < 1 || nt < 1 || leaf < 1 || !(theta > 0)) return NULL;
   for (int64_t i = 0; i < 4 * nt; i++)
@@ -533,7 +536,18 @@ oracle_tree* oracle_tree_build_sources(const double* nodes, int64_t nn, const in
   t->nt = nt;
   t->leaf = leaf;
   t->theta = theta;
-  t->dipoles = dipoles ? 1 : 0;
+  t->dipoles = sources == 1;
+  t->patches = sources == 2;
+  if (t->patches) { /* node -> incident tets */
+    t->nt_off = calloc(nn + 1, sizeof(int64_t));
+    for (int64_t q = 0; q < 4 * nt; q++) t->nt_off[tets[q] + 1]++;
+    for (int64_t i = 0; i < nn; i++) t->nt_off[i + 1] += t->nt_off[i];
+    int64_t* fill = malloc(sizeof(int64_t) * (nn + 1));
+    memcpy(fill, t->nt_off, sizeof(int64_t) * (nn + 1));
+    t->nt_tet = malloc(sizeof(int64_t) * 4 * nt);
+    for (int64_t q = 0; q < 4 * nt; q++) t->nt_tet[fill[tets[q]]++] = q / 4;
+    free(fill);
+  }
   if (t->dipoles) { /* lumped nodal volumes: a quarter of each incident tet */
     double* vol = malloc(sizeof(double) * nt);
     oracle_tet_volumes(nodes, tets, nt, vol);
@@ -647,6 +661,17 @@ oracle_tree* oracle_tree_build_sources(const double* nodes, int64_t nn, const in
       double d = dist3(nodes + 3 * t->node_perm[i], t->centre + 3 * c);
       if (d > rt) rt = d;
     }
+    if (t->patches) { /* a vertex patch reaches every vertex of the tets around its node */
+      rs = 0;
+      for (int64_t i = t->nb[c]; i < t->ne[c]; i++) {
+        const int64_t g = t->node_perm[i];
+        for (int64_t e = t->nt_off[g]; e < t->nt_off[g + 1]; e++)
+          for (int k = 0; k < 4; k++) {
+            double d = dist3(nodes + 3 * (int64_t)tets[4 * t->nt_tet[e] + k], t->centre + 3 * c);
+            if (d > rs) rs = d;
+          }
+      }
+    }
     t->r_src[c] = t->dipoles ? rt : rs; /* dipoles sit at the cell's own nodes */
     t->r_tgt[c] = rt;
   }
@@ -690,6 +715,8 @@ void oracle_tree_free(oracle_tree* t) {
   free(t->centre); free(t->r_src); free(t->r_tgt);
   free(t->m2l_off); free(t->m2l_src); free(t->p2p_off); free(t->p2p_src);
   free(t->node_vol);
+  free(t->nt_off);
+  free(t->nt_tet);
   free(t);
 }
 
@@ -820,10 +847,33 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
       }
     }
   }
+  /* P2M of vertex patches: the exact moments of lambda_j M_j over every tet around node j */
+  if (t->patches) {
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < ncell; c++) {
+      if (!is_leaf(t, c) || t->ne[c] == t->nb[c]) continue;
+      double* q = malloc(sizeof(double) * nc);
+      for (int b = 0; b < B; b++) {
+        double* Qc = Q + ((size_t)b * ncell + c) * nc;
+        for (int64_t i = t->nb[c]; i < t->ne[c]; i++) {
+          const int64_t g = t->node_perm[i];
+          for (int64_t e = t->nt_off[g]; e < t->nt_off[g + 1]; e++) {
+            double v[12], Mt[12];
+            gather_tet(t, t->nt_tet[e], M, b, v, Mt);
+            for (int k = 0; k < 4; k++)
+              if (t->tets_c[4 * t->nt_tet[e] + k] != g) Mt[3 * k] = Mt[3 * k + 1] = Mt[3 * k + 2] = 0;
+            tet_moments_tab(&T, &G, v, Mt, t->centre + 3 * c, q);
+            for (int m = 0; m < nc; m++) Qc[m] += q[m];
+          }
+        }
+      }
+      free(q);
+    }
+  }
   /* P2M: leaves holding tets */
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t c = 0; c < ncell; c++) {
-    if (t->dipoles || !is_leaf(t, c) || t->te[c] == t->tb[c]) continue;
+    if (t->dipoles || t->patches || !is_leaf(t, c) || t->te[c] == t->tb[c]) continue;
     double* q = malloc(sizeof(double) * nc);
     for (int b = 0; b < B; b++) {
       double* Qc = Q + ((size_t)b * ncell + c) * nc;
@@ -893,6 +943,19 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
               const double d0 = r[0] - rj[0], d1 = r[1] - rj[1], d2 = r[2] - rj[2];
               const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
               un += t->node_vol[j] * (mj[0] * d0 + mj[1] * d1 + mj[2] * d2) / (R2 * sqrt(R2));
+            }
+            continue;
+          }
+          if (t->patches) { /* lambda_j M_j over the tets around each source node j */
+            for (int64_t jj = t->nb[s]; jj < t->ne[s]; jj++) {
+              const int64_t j = t->node_perm[jj];
+              for (int64_t e = t->nt_off[j]; e < t->nt_off[j + 1]; e++) {
+                double v[12], Mt[12];
+                gather_tet(t, t->nt_tet[e], M, b, v, Mt);
+                for (int k = 0; k < 4; k++)
+                  if (t->tets_c[4 * t->nt_tet[e] + k] != j) Mt[3 * k] = Mt[3 * k + 1] = Mt[3 * k + 2] = 0;
+                un += oracle_tet_potential(r, v, Mt);
+              }
             }
             continue;
           }

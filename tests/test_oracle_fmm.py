@@ -254,3 +254,21 @@ def test_fmm_target_leaf_sample_matches_full(orc):
     part = tr.fmm(M, 4, target_leaves=leaves)
     sel = np.concatenate([ex["node_perm"][ex["cell_ranges"][c, 2]:ex["cell_ranges"][c, 3]] for c in leaves])
     assert np.array_equal(part[sel], full[sel])
+
+
+def test_vertex_patch_clustering(orc):
+    """The paper's clustering (sources = vertex patches lambda_i M_i, binned by node,
+    radius to the farthest vertex of the patch): the same u as the direct sum when
+    every pair is near, and a truncation error that falls with p like the tet
+    clustering's."""
+    nodes, tets = inputs.sphere(h=0.2)
+    M = inputs.gaussian_unit_m(nodes.shape[0], seed=9)
+    ref = orc.direct(nodes, tets, M)
+    u0 = orc.Tree(nodes, tets, 16, 1e-9, sources="patches").fmm(M, 4)
+    assert np.linalg.norm(u0 - ref) / np.linalg.norm(ref) < 1e-12
+    err = {}
+    for src in ("tets", "patches"):
+        err[src] = [np.linalg.norm(orc.Tree(nodes, tets, 16, 0.5, sources=src).fmm(M, p) - ref) / np.linalg.norm(ref)
+                    for p in (4, 8)]
+    assert err["patches"][0] > 10 * err["patches"][1]
+    assert err["patches"][1] < 3 * err["tets"][1], err
