@@ -427,11 +427,12 @@ int oracle_direct(const double* nodes, int64_t n_nodes, const int32_t* tets, int
   if (!nodes || !tets || !M || !u || B < 1) return 1;
   if (!targets && n_targets != n_nodes) return 1;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* thread count of this call only (a num_threads clause, not a global setting) */
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
   (void)nthreads;
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
   for (int64_t i = 0; i < n_targets; i++) {
     int64_t node = targets ? targets[i] : i;
     const double* r = nodes + 3 * node;
@@ -467,11 +468,12 @@ int oracle_direct_charges(const double* nodes, int64_t n_nodes, const int32_t* t
   if (!nodes || !tets || !M || !u || B < 1 || (n_bfaces && !bfaces)) return 1;
   if (!targets && n_targets != n_nodes) return 1;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* thread count of this call only (a num_threads clause, not a global setting) */
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
   (void)nthreads;
 #endif
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
   for (int64_t i = 0; i < n_targets; i++) {
     const int64_t node = targets ? targets[i] : i;
     const double* r = nodes + 3 * node;

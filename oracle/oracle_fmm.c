@@ -788,7 +788,8 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
                     int64_t n_target_leaves, int nthreads) {
   if (!t || !M || !u || B < 1 || p < 1 || p > 14) return 1;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* thread count of this call only (a num_threads clause, not a global setting) */
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
   (void)nthreads;
 #endif
@@ -821,7 +822,7 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
 
   /* P2M of point dipoles: Q_n = sum_i V_i M_i . grad(y^n) at y_i = r_i - c, leaves holding nodes */
   if (t->dipoles) {
-#pragma omp parallel for schedule(dynamic, 8)
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
     for (int64_t c = 0; c < ncell; c++) {
       if (!is_leaf(t, c) || t->ne[c] == t->nb[c]) continue;
       for (int b = 0; b < B; b++) {
@@ -849,7 +850,7 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
   }
   /* P2M of vertex patches: the exact moments of lambda_j M_j over every tet around node j */
   if (t->patches) {
-#pragma omp parallel for schedule(dynamic, 8)
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
     for (int64_t c = 0; c < ncell; c++) {
       if (!is_leaf(t, c) || t->ne[c] == t->nb[c]) continue;
       double* q = malloc(sizeof(double) * nc);
@@ -871,7 +872,7 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
     }
   }
   /* P2M: leaves holding tets */
-#pragma omp parallel for schedule(dynamic, 8)
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
   for (int64_t c = 0; c < ncell; c++) {
     if (t->dipoles || t->patches || !is_leaf(t, c) || t->te[c] == t->tb[c]) continue;
     double* q = malloc(sizeof(double) * nc);
@@ -897,7 +898,7 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
       }
   }
   /* M2L */
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
   for (int64_t c = 0; c < ncell; c++) {
     if (!mark[c]) continue;
     double* D = malloc(sizeof(double) * nc);
@@ -922,7 +923,7 @@ int oracle_fmm_eval(const oracle_tree* t, int p, const double* M, int B, double*
     }
   }
   /* L2P + P2P per target leaf */
-#pragma omp parallel for schedule(dynamic, 2)
+#pragma omp parallel for schedule(dynamic, 2) num_threads(nt)
   for (int64_t li = 0; li < nleaves; li++) {
     int64_t c = leaves[li];
     for (int64_t i = t->nb[c]; i < t->ne[c]; i++) {
