@@ -119,14 +119,39 @@ typedef struct {
                           volume) with the Laplace kernel and the same tree,
                           lists and translations -- the node-dipole
                           comparison the paper makes (Sec. 4); needs
-                          near_mode = 1                                    */
+                          near_mode = 1.  DEMAG_SOURCES_PATCHES (2): the
+                          paper's own clustering (Sec. 2.1, 3.1-3.2): node i
+                          carries lambda_i M over every tet around it, is
+                          binned by its own key, and a cell's source radius
+                          reaches the farthest vertex of the tets around its
+                          nodes; exact patch moments and analytic patch near
+                          field; the same u as the tets up to the FMM
+                          truncation; needs near_mode = 1                  */
+  int near_tc;         /* DEMAG_MIXED_BF16X3 with near_mode = 1: 0
+                          (default) applies the stored near-field
+                          coefficients (Sec. 3.4) on the tensor cores --
+                          tiles of up to 128 target nodes over the union of
+                          their source columns, coefficients and M in two
+                          BF16 limbs (16 significant bits; up to ~1e-5
+                          relative error per product), three MMAs per
+                          k-step, FP32 accumulation; < 0: FP32 CUDA cores,
+                          as in the other mixed precisions (BF16X6 always) */
+  int graph;           /* 1: demag_eval with device pointers (and profile =
+                          0) runs the first call with a given (M, u, H,
+                          batch, workspace) directly, records it as a CUDA
+                          graph and replays that graph with one launch on
+                          later calls with the same pointers (as
+                          demag_eval_multi does for several plans; launch
+                          arguments, including demag_plan_debug flags, are
+                          those of the recorded call); 0 (default): every
+                          call launches its kernels                         */
 } demag_options;
 
-enum { DEMAG_SOURCES_TETS = 0, DEMAG_SOURCES_DIPOLES = 1 };
+enum { DEMAG_SOURCES_TETS = 0, DEMAG_SOURCES_DIPOLES = 1, DEMAG_SOURCES_PATCHES = 2 };
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
  * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0,
- * m2l_table_batch=0, sources=0. */
+ * m2l_table_batch=0, sources=0, near_tc=0, graph=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and
@@ -161,6 +186,20 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
  * Nodes that belong to no tet get their potential, and H = 0. */
 demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream);
 
+/* Device-side status of the most recent evaluation of `plan` (demag_eval,
+ * demag_eval_noalloc, or this plan's part of a demag_eval_multi submission).
+ * Calls with device pointers are asynchronous, so a bounded device wait that
+ * expires in one of their kernels cannot be reported by the call itself; the
+ * kernel records it in a device flag instead.  This synchronises cuda_stream
+ * (the stream the evaluation was issued on) and returns DEMAG_ERR_TIMEOUT if
+ * that flag is set -- the outputs of that evaluation are then unspecified and
+ * the plan stays valid -- else DEMAG_OK (also for a plan never evaluated).
+ * Host-pointer calls of demag_eval check the flag themselves.  The flag of
+ * demag_eval_noalloc lives in the shared fixed scratch area and is cleared by
+ * the next demag_eval_noalloc call on the same device, so query it before that
+ * call.  Errors: DEMAG_ERR_INVALID_ARG (NULL plan), DEMAG_ERR_CUDA. */
+demag_status demag_eval_status(demag_plan plan, void* cuda_stream);
+
 /* Size of the fixed scratch area used by demag_eval_noalloc (64 MiB). */
 #define DEMAG_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
 
@@ -178,10 +217,14 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
  *                 as demag_eval.  The call is asynchronous on cuda_stream.
  * Errors: DEMAG_ERR_INVALID_ARG for NULL or host pointers, batch < 1, or a plan
  * and batch whose scratch exceeds DEMAG_NOALLOC_SCRATCH_BYTES (the message gives
- * both sizes); DEMAG_ERR_CUDA if the scratch address cannot be resolved.
+ * both sizes); DEMAG_ERR_CUDA if the scratch address cannot be resolved.  A
+ * bounded device wait that expires in the kernels is not seen by this
+ * asynchronous call: check demag_eval_status before the next call.
  * The first call on a device resolves the array's device address with that
  * device current (one cudaGetSymbolAddress), so make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the last
+ * stream capture.  The address is kept per device and CUDA context: a call
+ * under a different context of the device (for instance after
+ * cudaDeviceReset) resolves it again.  All calls on a device share the array and it keeps the last
  * call's contents (each call clears what must start at zero); calls that
  * overlap on the GPU race on it and must be serialised by the caller.
  * With opt.profile = 1 the stage timers are not updated by this entry point. */
@@ -238,6 +281,17 @@ demag_status demag_llg_rk4(demag_plan plan, double* m, int batch, double Ms, dou
 
 demag_status demag_plan_destroy(demag_plan plan);
 
+/* Test hook for the error path of the bounded device waits (the paper has no
+ * counterpart).  flags bit 0: the tensor-core near field (DEMAG_MIXED_BF16X3,
+ * near_mode = 1) issues none of its coefficient copies, so its MMA issuer's
+ * bounded wait for them expires (after about a second) with no copy and no MMA
+ * in flight; the kernel records DEMAG_ERR_TIMEOUT, frees its tensor memory and
+ * returns.  demag_eval then returns DEMAG_ERR_TIMEOUT for host pointers, and
+ * demag_eval_status reports it for device pointers; the plan and the CUDA
+ * context stay usable.  flags = 0 restores normal evaluation.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL plan, unknown flag bits). */
+demag_status demag_plan_debug(demag_plan plan, int flags);
+
 /* Stages of demag_eval, for the per-stage timers. */
 enum {
   DEMAG_STAGE_GATHER = 0, /* M to the sorted, state-innermost layout          */
@@ -276,6 +330,11 @@ typedef struct {
   int m2l_ring_bytes;    /* tensor-core M2L ring: shared memory per CTA     */
   int m2l_targets_per_cta; /* tensor-core M2L: target cells sharing each
                             source's moments in one CTA (1 or 2)            */
+  int64_t n_near_tiles;  /* tiles of the tensor-core near field (0: none)   */
+  int64_t near_tile_cols; /* columns of those tiles, summed (groups of 16)  */
+  int64_t near_bytes;    /* bytes of stored near-field coefficients read by
+                            one evaluation of up to 256 states (FP64, FP32
+                            or split-BF16 layout, whichever the plan holds) */
 } demag_stats;
 
 demag_status demag_plan_stats(demag_plan plan, demag_stats* out);
@@ -307,6 +366,18 @@ typedef struct {
 } demag_tree_export;
 
 demag_status demag_plan_export_tree(demag_plan plan, demag_tree_export* out);
+
+/* Measured arithmetic peak of the current device, for stating roofline
+ * fractions against a reproducible denominator (the paper has no counterpart):
+ *   kind 0: FP64 FMA on the CUDA cores, 1: FP32 FMA on the CUDA cores,
+ *   2: BF16 tcgen05.mma (M = 128, N = 256, K = 16, FP32 accumulation),
+ *   3: TF32 tcgen05.mma (M = 128, N = 256, K = 8).
+ * Register-resident FMA chains on every SM, or one CTA per SM issuing MMAs on
+ * shared-memory operands; 2 flops per multiply-add; best of three timed runs
+ * after a warm-up (CUDA events, a private stream).  *tflops receives TFLOP/s.
+ * Synchronous; takes up to a second.
+ * Errors: DEMAG_ERR_INVALID_ARG, DEMAG_ERR_CUDA, DEMAG_ERR_TIMEOUT. */
+demag_status demag_measure_peak(int kind, double* tflops);
 
 const char* demag_status_string(demag_status s);
 /* Message of the last failing call on this thread ("" if none). */

@@ -374,3 +374,42 @@ class Tree:
         if rc:
             raise RuntimeError("oracle_fmm_eval failed")
         return u[0] if squeeze else u
+
+
+# ---- energy and LLG stepping (uses of H next to the potential, Sec. 4.1-4.2) -----
+def energy(nodes, tets, M, H):
+    """Magnetostatic self-energy per state, e = -(1/2) sum_i V_i M_i . H_i with the
+    lumped nodal volumes V_i of the mass-lumped H (E = mu0 e).  M, H: (N_n, 3) or
+    (B, N_n, 3); plain numpy."""
+    V = lumped_volumes(nodes, tets)
+    M, H = np.asarray(M, dtype=np.float64), np.asarray(H, dtype=np.float64)
+    return -0.5 * np.einsum("i,...ik,...ik->...", V, M, H)
+
+
+def llg_rhs(m, h, alpha):
+    """Landau-Lifshitz-Gilbert right-hand side in reduced units,
+    dm/dt = -1/(1 + alpha^2) [ m x h + alpha m x (m x h) ], row by row (..., 3)."""
+    mxh = np.cross(m, h)
+    return -(mxh + alpha * np.cross(m, mxh)) / (1.0 + alpha * alpha)
+
+
+def rk4_step(f, y, dt):
+    """One classical fourth-order Runge-Kutta step of dy/dt = f(y)."""
+    k1 = f(y)
+    k2 = f(y + 0.5 * dt * k1)
+    k3 = f(y + 0.5 * dt * k2)
+    k4 = f(y + dt * k3)
+    return y + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+
+def llg_rk4(m, field, Ms, alpha, h_ext, dt, steps):
+    """`steps` RK4 steps of the reduced LLG equation for unit states m (B, N_n, 3):
+    h = field(Ms y) / Ms + h_ext at every stage state y, where field(M) returns the
+    demagnetising field H (B, N_n, 3) of the magnetisation M; m renormalised to
+    unit length after each step.  Returns the new m."""
+    m = np.array(m, dtype=np.float64)
+    hx = np.zeros(3) if h_ext is None else np.asarray(h_ext, dtype=np.float64)
+    for _ in range(steps):
+        m = rk4_step(lambda y: llg_rhs(y, field(Ms * y) / Ms + hx, alpha), m, dt)
+        m /= np.linalg.norm(m, axis=-1, keepdims=True)
+    return m

@@ -30,7 +30,8 @@ class demag_options(C.Structure):
                 ("near_mode", C.c_int), ("max_batch", C.c_int), ("autotune", C.c_int), ("profile", C.c_int),
                 ("m2l_targets_per_cta", C.c_int), ("m2l_kps", C.c_int),
                 ("m2l_promote", C.c_int), ("m2l_promote_rows", C.c_int),
-                ("m2l_table_batch", C.c_int), ("sources", C.c_int)]
+                ("m2l_table_batch", C.c_int), ("sources", C.c_int), ("near_tc", C.c_int),
+                ("graph", C.c_int)]
 
 
 DEMAG_N_STAGES = 9
@@ -46,7 +47,8 @@ class demag_stats(C.Structure):
                 ("theta", C.c_double), ("eval_launches", C.c_int64), ("n_evals_profiled", C.c_int64),
                 ("stage_ms", C.c_double * DEMAG_N_STAGES), ("stage_launches", C.c_int64 * DEMAG_N_STAGES),
                 ("n_m2l_ops", C.c_int64), ("m2l_kps", C.c_int), ("m2l_ring_bytes", C.c_int),
-                ("m2l_targets_per_cta", C.c_int)]
+                ("m2l_targets_per_cta", C.c_int), ("n_near_tiles", C.c_int64), ("near_tile_cols", C.c_int64),
+                ("near_bytes", C.c_int64)]
 
 
 class demag_tree_export(C.Structure):
@@ -79,6 +81,10 @@ def load(build_if_missing: bool = True):
         L.demag_plan_create.argtypes = [vp, i64, vp, i64, i32, i32, d, C.POINTER(demag_options), C.POINTER(vp)]
         L.demag_eval.restype = i32
         L.demag_eval.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.demag_plan_debug.restype = i32
+        L.demag_plan_debug.argtypes = [vp, i32]
+        L.demag_eval_status.restype = i32
+        L.demag_eval_status.argtypes = [vp, vp]
         L.demag_eval_noalloc.restype = i32
         L.demag_eval_noalloc.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_eval_multi.restype = i32
@@ -95,6 +101,8 @@ def load(build_if_missing: bool = True):
         L.demag_plan_reset_timers.argtypes = [vp]
         L.demag_plan_export_tree.restype = i32
         L.demag_plan_export_tree.argtypes = [vp, C.POINTER(demag_tree_export)]
+        L.demag_measure_peak.restype = i32
+        L.demag_measure_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.demag_status_string.restype = C.c_char_p
         L.demag_status_string.argtypes = [i32]
         L.demag_last_error.restype = C.c_char_p
@@ -118,6 +126,16 @@ def demag_plan_create(nodes_ptr, n_nodes, tets_ptr, n_tets, p, leaf_size, theta,
 
 def demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
     return load().demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr)
+
+
+def demag_eval_status(plan, stream_ptr):
+    """DEMAG_ERR_TIMEOUT if a bounded device wait expired in the plan's last evaluation (synchronises)."""
+    return load().demag_eval_status(plan, stream_ptr)
+
+
+def demag_plan_debug(plan, flags):
+    """Test hook: bit 0 stalls the tensor-core near field so that its bounded wait expires."""
+    return load().demag_plan_debug(plan, flags)
 
 
 def demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
@@ -154,6 +172,16 @@ def demag_plan_reset_timers(plan):
 
 def demag_plan_export_tree(plan, out: demag_tree_export):
     return load().demag_plan_export_tree(plan, C.byref(out))
+
+
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "bf16_mma": 2, "tf32_mma": 3}
+
+
+def demag_measure_peak(kind: int) -> tuple[int, float]:
+    """Measured TFLOP/s of one arithmetic path of the current device (see include/demag.h)."""
+    v = C.c_double(0.0)
+    st = load().demag_measure_peak(int(kind), C.byref(v))
+    return st, float(v.value)
 
 
 def demag_status_string(status: int) -> str:

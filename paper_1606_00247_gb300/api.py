@@ -32,7 +32,7 @@ class Plan:
 
     def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
                  device="cuda", profile=False, autotune=False, m2l_targets_per_cta=0, m2l_kps=0,
-                 m2l_promote=0, m2l_promote_rows=0, m2l_table_batch=0, sources="tets"):
+                 m2l_promote=0, m2l_promote_rows=0, m2l_table_batch=0, sources="tets", near_tc=0, graph=False):
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
@@ -48,7 +48,9 @@ class Plan:
         opt.m2l_promote = int(m2l_promote)
         opt.m2l_promote_rows = int(m2l_promote_rows)
         opt.m2l_table_batch = int(m2l_table_batch)
-        opt.sources = {"tets": 0, "dipoles": 1}[sources] if isinstance(sources, str) else int(sources)
+        opt.sources = {"tets": 0, "dipoles": 1, "patches": 2}[sources] if isinstance(sources, str) else int(sources)
+        opt.near_tc = int(near_tc)
+        opt.graph = int(bool(graph))  # demag_eval with device pointers: record once, replay as a CUDA graph
         with torch.cuda.device(self.device):
             st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
                                         int(leaf_size), float(theta), opt)

@@ -307,6 +307,8 @@ void demag_options_default(demag_options* o) {
   o->m2l_table_batch = 0;
   o->sources = DEMAG_SOURCES_TETS;
   o->profile = 0;
+  o->near_tc = 0;
+  o->graph = 0;
 }
 
 demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, int p,
@@ -334,12 +336,13 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
     if (o.m2l_promote_rows < 0 || o.m2l_promote_rows > 64) fail(DEMAG_ERR_INVALID_ARG, "m2l_promote_rows must be in 0..64");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
-    if (o.sources != DEMAG_SOURCES_TETS && o.sources != DEMAG_SOURCES_DIPOLES)
-      fail(DEMAG_ERR_INVALID_ARG, "sources must be DEMAG_SOURCES_TETS or DEMAG_SOURCES_DIPOLES");
-    if (o.sources == DEMAG_SOURCES_DIPOLES && o.near_mode != 1)
-      fail(DEMAG_ERR_UNSUPPORTED, "point-dipole sources need near_mode = 1");
+    if (o.sources != DEMAG_SOURCES_TETS && o.sources != DEMAG_SOURCES_DIPOLES && o.sources != DEMAG_SOURCES_PATCHES)
+      fail(DEMAG_ERR_INVALID_ARG, "sources must be DEMAG_SOURCES_TETS, _DIPOLES or _PATCHES");
+    if (o.sources != DEMAG_SOURCES_TETS && o.near_mode != 1)
+      fail(DEMAG_ERR_UNSUPPORTED, "point-dipole and vertex-patch sources need near_mode = 1");
     if (o.precision < DEMAG_FP64 || o.precision > DEMAG_MIXED_BF16X6)
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
+    if (o.graph != 0 && o.graph != 1) fail(DEMAG_ERR_INVALID_ARG, "graph must be 0 or 1");
     const auto t0 = std::chrono::steady_clock::now();
     if (o.autotune & 4) {
       o.p = tune_p(o, n_nodes, n_tets, nodes, tets);
@@ -360,11 +363,42 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
   return guarded([&] {
     if (!plan || !M || !u) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
     if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
+    if (plan->opt.graph && !plan->opt.profile && is_device_ptr(M) && is_device_ptr(u) && (!H || is_device_ptr(H))) {
+      Plan* pp = plan;
+      eval_multi(&pp, 1, &M, &batch, &u, H ? &H : nullptr, (cudaStream_t)cuda_stream);  // record once, replay
+      return;
+    }
     if (plan->opt.precision == DEMAG_FP64)
       eval_fp64(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
     else
       eval_mixed(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
   });
+}
+
+demag_status demag_plan_debug(demag_plan plan, int flags) {
+  if (!plan || (flags & ~1)) {
+    set_last_error("demag_plan_debug: NULL plan or unknown flag bits");
+    return DEMAG_ERR_INVALID_ARG;
+  }
+  plan->debug_flags = flags;
+  return DEMAG_OK;
+}
+
+demag_status demag_eval_status(demag_plan plan, void* cuda_stream) {
+  int herr = 0;
+  demag_status st = guarded([&] {
+    if (!plan) fail(DEMAG_ERR_INVALID_ARG, "NULL plan");
+    if (!plan->last_err) return;  // never evaluated
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    DM_CUDA(cudaMemcpyAsync(&herr, plan->last_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != DEMAG_OK) return st;
+  if (herr == DEMAG_ERR_TIMEOUT) {
+    set_last_error("a bounded device wait expired in the last evaluation of this plan; its outputs are unspecified");
+    return DEMAG_ERR_TIMEOUT;
+  }
+  return herr ? DEMAG_ERR_CUDA : DEMAG_OK;
 }
 
 demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double* const* M, const int* batch,
@@ -455,6 +489,11 @@ demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
   o->m2l_kps = plan->tc_kps;
   o->m2l_ring_bytes = plan->tc_budget;
   o->m2l_targets_per_cta = plan->tc_ops ? plan->tc_nt : 0;
+  o->n_near_tiles = plan->nf_ntiles;
+  o->near_tile_cols = plan->nf_ncols;
+  o->near_bytes = plan->nf_W ? plan->nf_wbytes
+                             : (plan->W32 ? plan->n_wentries / 3 * 16
+                                          : (plan->W64 ? plan->n_wentries * 8 : 0));
   return DEMAG_OK;
 }
 

@@ -29,6 +29,7 @@ constexpr int KEY_BITS = 21;
 constexpr int MAX_LEVEL = 20;
 constexpr int MAX_P = 12;
 constexpr int MAX_NCOEF = (MAX_P + 1) * (MAX_P + 2) * (MAX_P + 3) / 6;  // 455
+constexpr int NF_ROWS = 128;  // target nodes per tile of the tensor-core near field (MMA N <= 128)
 
 __host__ __device__ inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -167,6 +168,20 @@ struct Plan {
   int64_t* w_off32 = nullptr;       // nT + 1, in floats; W32 is [col][node][4]
   float* W32 = nullptr;
 
+  // the same coefficients for the tensor-core near field (split-BF16
+  // precisions, near_mode = 1; near_tc.cu): tiles of at most NF_ROWS target
+  // nodes of consecutive P2P target leaves (leaves ordered by first node), the
+  // union of their columns in groups of 16, W in split BF16 per k-step
+  // (group, component) in the tensor-core K-major layout
+  int64_t nf_ntiles = 0, nf_ncols = 0, nf_wbytes = 0;
+  int64_t* nf_woff = nullptr;       // ntiles: byte offset of the tile in nf_W
+  int64_t* nf_coff = nullptr;       // ntiles: first column of the tile in nf_cols
+  int32_t* nf_ng = nullptr;         // ntiles: column groups of 16
+  int32_t* nf_npad = nullptr;       // ntiles: rows padded to 16
+  int32_t* nf_rownode = nullptr;    // ntiles x NF_ROWS: sorted node of each row, -1 = none
+  int32_t* nf_cols = nullptr;       // sorted node of each column (groups padded with the last column)
+  unsigned char* nf_W = nullptr;
+
   // tensor-core M2L (TF32 / split BF16): one operator tile set per distinct
   // (level difference, lattice offset) and the operator index of every pair
   int64_t n_tc_ops = 0;
@@ -208,6 +223,8 @@ struct Plan {
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
   Workspace* ws = nullptr;
+  int* last_err = nullptr;          // device error flag of the most recent evaluation (demag_eval_status)
+  int debug_flags = 0;              // demag_plan_debug: test hooks (bit 0: near-field stall)
 
   // per-stage timers (opt.profile) and launch counts
   double stage_ms[DEMAG_N_STAGES] = {};
@@ -262,6 +279,7 @@ struct Workspace {
   double *Ms = nullptr, *Q = nullptr, *L = nullptr, *u_s = nullptr, *state = nullptr;
   float *Ms32 = nullptr, *Q32 = nullptr, *L32 = nullptr, *u32 = nullptr;
   unsigned char* QP = nullptr;  // moments in the tensor-core tile layout (TF32 / split BF16 M2L)
+  float* MP = nullptr;          // tensor-core near field: M per 128-state block, [block][node][3][128]
   double *M_dev = nullptr, *u_dev = nullptr, *H_dev = nullptr;  // staging for host pointers
   int* err = nullptr;
   std::vector<void*> ptrs;
@@ -285,6 +303,11 @@ void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H
 void build_near_field(Plan& P);
 void launch_near_apply64(Plan& P, const double* Ms, int B, double* u_s, cudaStream_t s);
 void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, cudaStream_t s);
+// tensor-core near field (near_tc.cu): used when the plan holds the tiles
+bool near_tc_wanted(const Plan& P);
+// MP: workspace of nf_mp_floats(P, B) floats for M in the layout of the kernel's bulk copies
+size_t nf_mp_floats(const Plan& P, int B);
+void launch_near_tc(Plan& P, const float* Ms, float* MP, int B, float* u_s, int* err, cudaStream_t s);
 struct M2lKeys {  // distinct translation keys (dl, lattice offset) and the key of every M2L pair
   bool ok = false;
   std::vector<int4> keys;

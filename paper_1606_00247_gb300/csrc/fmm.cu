@@ -328,6 +328,8 @@ Workspace& workspace(Plan& P, int B) {
     W->u32 = (float*)ws_alloc(*W, sizeof(float) * nn * need);
     const size_t qp = m2l_tc_pack_bytes(P, need);
     if (qp) W->QP = (unsigned char*)ws_alloc(*W, qp);
+    const size_t mp = nf_mp_floats(P, need);
+    if (mp) W->MP = (float*)ws_alloc(*W, sizeof(float) * mp);
   }
   if (!mixed || otf) W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);  // FP64 sorted u
   if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);
@@ -469,6 +471,7 @@ bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, dou
     *Hd = H ? W.H_dev : nullptr;
   }
   DM_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), s));
+  P.last_err = W.err;
   return dev;
 }
 

@@ -501,7 +501,10 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
     near_field_fp64(P, W, B, clk, s);
   } else {
     clk.begin(DEMAG_STAGE_P2P);
-    if (!P.h_p2p_targets.empty()) {
+    if (P.nf_W) {
+      launch_near_tc(P, W.Ms32, W.MP, B, W.u32, W.err, s);
+      clk.launched();
+    } else if (!P.h_p2p_targets.empty()) {
       launch_near_apply32(P, W.Ms32, B, W.u32, W.err, s);
       clk.launched();
     }

@@ -10,8 +10,10 @@
 // evaluation the near field is then a block-sparse product with the nodal M
 // of all B states (FP64 for the FP64 path, FP32 for the mixed paths).
 #include <cub/cub.cuh>
+#include <cuda_bf16.h>
 
 #include <algorithm>
+#include <memory>
 
 #include "common.cuh"
 #include "p2p.cuh"
@@ -100,6 +102,64 @@ __global__ void __launch_bounds__(128) k_near_build_dipole(const int32_t* __rest
   }
 }
 
+// vertex-patch near field: W[col j][target i] = 1/(4 pi) sum_{t ni j} int_t lambda_j(r') (r_i - r') / |r_i - r'|^3 dV'
+// over every tet around each own node j of the P2P source leaves (one block per
+// target leaf; (target, tet around j) pairs over threads; a tet around several
+// source nodes is integrated once per node).  W holds 64-bit integers in units
+// of 1 / fix while it is being built (see k_fixed_to_double).
+__global__ void __launch_bounds__(128) k_near_build_patch(
+    const int32_t* __restrict__ targets, const int4* __restrict__ range, const int64_t* __restrict__ p2p_off,
+    const int32_t* __restrict__ p2p_src, const double* __restrict__ nodes_s, const int32_t* __restrict__ tets_s,
+    const double* __restrict__ geo, const double* __restrict__ grad, const int64_t* __restrict__ nt_off,
+    const int32_t* __restrict__ nt_tet, const int64_t* __restrict__ coloff, const int32_t* __restrict__ cols,
+    const int64_t* __restrict__ woff, double fix, unsigned long long* W) {
+  const int64_t ti = blockIdx.x;
+  const int32_t T = targets[ti];
+  const int4 rT = range[T];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = coloff[ti], ncol = coloff[ti + 1] - c0;
+  unsigned long long* Wt = W + woff[ti];
+  const double scl = fix / (4.0 * M_PI);
+  for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
+    const int4 rS = range[p2p_src[e]];
+    for (int32_t j = rS.z; j < rS.w; j++) {
+      int64_t lo = 0, hi = ncol;  // column of node j
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cols[c0 + mid] < j)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      const int64_t t0 = nt_off[j];
+      const int deg = (int)(nt_off[j + 1] - t0);
+      for (int q = threadIdx.x; q < nT * deg; q += blockDim.x) {
+        const int i = q / deg;
+        const int32_t t = nt_tet[t0 + (q - i * deg)];
+        const double* r = nodes_s + 3ll * (rT.z + i);
+        const double* G = geo + (int64_t)t * TET_GEO;
+        PairAT at;
+        pair_at(G, r[0], r[1], r[2], at);
+        int k = 0;
+        while (k < 3 && tets_s[4ll * t + k] != j) k++;
+        const double* g = grad + 12ll * t;
+        const double d0 = r[0] - G[0], d1 = r[1] - G[1], d2 = r[2] - G[2];
+        const double l1 = g[3] * d0 + g[4] * d1 + g[5] * d2, l2 = g[6] * d0 + g[7] * d1 + g[8] * d2,
+                     l3 = g[9] * d0 + g[10] * d1 + g[11] * d2;
+        const double lam = k == 0 ? 1.0 - l1 - l2 - l3 : (k == 1 ? l1 : (k == 2 ? l2 : l3));
+        const double gx = g[3 * k], gy = g[3 * k + 1], gz = g[3 * k + 2];
+        const double w0 = lam * at.a[0] + 0.5 * (at.T[0] * gx + at.T[3] * gy + at.T[4] * gz);
+        const double w1 = lam * at.a[1] + 0.5 * (at.T[3] * gx + at.T[1] * gy + at.T[5] * gz);
+        const double w2 = lam * at.a[2] + 0.5 * (at.T[4] * gx + at.T[5] * gy + at.T[2] * gz);
+        unsigned long long* dst = Wt + (lo * nT + i) * 3;
+        atomicAdd(dst, (unsigned long long)__double2ll_rn(w0 * scl));
+        atomicAdd(dst + 1, (unsigned long long)__double2ll_rn(w1 * scl));
+        atomicAdd(dst + 2, (unsigned long long)__double2ll_rn(w2 * scl));
+      }
+    }
+  }
+}
+
 __global__ void k_col_offsets(const uint64_t* __restrict__ keys, int64_t n, int64_t nT, int64_t* off, int32_t* cols) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c <= nT) {
@@ -120,7 +180,9 @@ __global__ void k_col_offsets(const uint64_t* __restrict__ keys, int64_t n, int6
 constexpr int NB_CHUNK = 32;
 constexpr int NB_COLCACHE = 4096;
 
-// one block per P2P target leaf; (target node, source tet) pairs over threads
+// one block per P2P target leaf; (target node, source tet) pairs over threads.
+// W holds 64-bit integers in units of 1 / fix while it is being built (see
+// k_fixed_to_double)
 __global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ targets, const int4* __restrict__ range,
                                                     const int64_t* __restrict__ p2p_off,
                                                     const int32_t* __restrict__ p2p_src,
@@ -129,7 +191,7 @@ __global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ 
                                                     const double* __restrict__ geo, const double* __restrict__ grad,
                                                     const int64_t* __restrict__ coloff,
                                                     const int32_t* __restrict__ cols, const int64_t* __restrict__ woff,
-                                                    double* W) {
+                                                    double fix, unsigned long long* W) {
   __shared__ double s_geo[NB_CHUNK * TET_GEO];
   __shared__ double s_grad[NB_CHUNK * 12];
   __shared__ int32_t s_node[NB_CHUNK * 4];
@@ -143,8 +205,8 @@ __global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ 
   if (cached)
     for (int64_t q = threadIdx.x; q < ncol; q += blockDim.x) s_cols[q] = cols[c0 + q];
   const int32_t* colv = cached ? s_cols : cols + c0;
-  double* Wt = W + woff[ti];
-  const double inv4pi = 1.0 / (4.0 * M_PI);
+  unsigned long long* Wt = W + woff[ti];
+  const double scl = fix / (4.0 * M_PI);
   for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
     const int4 rS = range[p2p_src[e]];
     for (int32_t j0 = rS.x; j0 < rS.y; j0 += NB_CHUNK) {
@@ -182,10 +244,11 @@ __global__ void __launch_bounds__(128) k_near_build(const int32_t* __restrict__ 
             else
               hi = mid;
           }
-          double* dst = Wt + (lo * nT + i) * 3;
-          atomicAdd(dst, w0 * inv4pi);
-          atomicAdd(dst + 1, w1 * inv4pi);
-          atomicAdd(dst + 2, w2 * inv4pi);
+          // integer sums: exact and independent of the order of the threads' additions
+          unsigned long long* dst = Wt + (lo * nT + i) * 3;
+          atomicAdd(dst, (unsigned long long)__double2ll_rn(w0 * scl));
+          atomicAdd(dst + 1, (unsigned long long)__double2ll_rn(w1 * scl));
+          atomicAdd(dst + 2, (unsigned long long)__double2ll_rn(w2 * scl));
         }
       }
     }
@@ -506,21 +569,164 @@ __global__ void __launch_bounds__(NB_WARPS * 32, 2) k_near_apply32_v3(
   }
 }
 
+// fixed-point coefficients -> FP64 (in place): the near-field build adds its
+// per-tet contributions as 64-bit integers in units of 1 / NEAR_FIX (exact,
+// order-independent sums), so the coefficients do not depend on the order in
+// which the threads add them
+__global__ void k_fixed_to_double(int64_t n, double* W, double inv) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const long long v = __double_as_longlong(W[q]);
+    W[q] = (double)v * inv;
+  }
+}
+
+// keys (tile << 32 | node) of the columns of every leaf of the chunk's tiles:
+// one block per tile, the leaves' (sorted, distinct) columns concatenated
+__global__ void k_nf_tile_keys(const int64_t* __restrict__ tleaf, const int64_t* __restrict__ tkoff,
+                               const int64_t* __restrict__ lcoloff, const uint64_t* __restrict__ lkeys, uint64_t* out) {
+  const int64_t t = blockIdx.x;
+  int64_t o = tkoff[t];
+  for (int64_t l = tleaf[2 * t]; l < tleaf[2 * t + 1]; l++) {
+    const int64_t c0 = lcoloff[l], n = lcoloff[l + 1] - c0;
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x)
+      out[o + q] = ((uint64_t)t << 32) | (uint32_t)(lkeys[c0 + q] & 0xffffffffu);
+    o += n;
+  }
+}
+
+// columns of each tile from its sorted distinct keys, padded to groups of 16 with the last column
+__global__ void k_nf_tile_cols(const uint64_t* __restrict__ keys, const int64_t* __restrict__ kofft,
+                               const int64_t* __restrict__ coff, int32_t* cols) {
+  const int64_t t = blockIdx.x;
+  const int64_t k0 = kofft[t], n = kofft[t + 1] - k0, npad = (n + 15) / 16 * 16;
+  int32_t* dst = cols + coff[t];
+  for (int64_t q = threadIdx.x; q < npad; q += blockDim.x)
+    dst[q] = (int32_t)(keys[k0 + (q < n ? q : n - 1)] & 0xffffffffu);
+}
+
+// split-BF16 tile coefficients from the per-leaf FP64 ones: one block per leaf;
+// every (row, column, component) of a tile is written by exactly one thread
+__global__ void k_nf_pack(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                          const int64_t* __restrict__ lcoloff, const int32_t* __restrict__ lcols,
+                          const int64_t* __restrict__ lwoff, const double* __restrict__ W,
+                          const int32_t* __restrict__ ltile, const int32_t* __restrict__ lrow0,
+                          const int64_t* __restrict__ twoff, const int64_t* __restrict__ tcoff,
+                          const int32_t* __restrict__ tng, const int32_t* __restrict__ tnpad,
+                          const int32_t* __restrict__ tcols, unsigned char* Wtc) {
+  const int64_t l = blockIdx.x;
+  const int4 rT = range[targets[l]];
+  const int nT = rT.w - rT.z;
+  const int64_t c0 = lcoloff[l], ncol = lcoloff[l + 1] - c0;
+  const double* Wl = W + lwoff[l];
+  for (int64_t q = threadIdx.x; q < ncol * nT; q += blockDim.x) {
+    const int64_t c = q / nT;
+    const int i = (int)(q - c * nT);
+    const int rr = lrow0[l] + i;
+    const int64_t t = ltile[l] + rr / NF_ROWS;
+    const int r = rr % NF_ROWS;
+    const int32_t node = lcols[c0 + c];
+    const int32_t* tc = tcols + tcoff[t];
+    int64_t lo = 0, hi = (int64_t)tng[t] * 16;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (tc[mid] < node)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int npad = tnpad[t];
+    unsigned char* base = Wtc + twoff[t];
+    for (int comp = 0; comp < 3; comp++) {
+      const double v = Wl[(c * nT + i) * 3 + comp];
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      const __nv_bfloat16 s = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+      const int64_t ks = 3 * (lo / 16) + comp;
+      const int k = (int)(lo % 16);
+      unsigned char* kb = base + ks * 64 * npad + (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+      *(__nv_bfloat16*)kb = h;
+      *(__nv_bfloat16*)(kb + 32 * npad) = s;
+    }
+  }
+}
+
 }  // namespace
 
+// Tiles of the tensor-core near field over the P2P target leaves (already in
+// order of their first node): consecutive leaves with at most NF_ROWS target
+// nodes together; a leaf with more nodes gets tiles of its own, NF_ROWS rows
+// each.
+struct NfTiles {
+  std::vector<int64_t> leaf;   // 2 per tile: its leaves [leaf0, leaf1)
+  std::vector<int32_t> nrow;   // rows per tile
+  std::vector<int32_t> ltile;  // per leaf: its first tile
+  std::vector<int32_t> lrow0;  // per leaf: row of its first node in that tile
+};
+
+static NfTiles nf_make_tiles(const Plan& P) {
+  NfTiles T;
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
+  T.ltile.resize(nT);
+  T.lrow0.resize(nT);
+  int64_t cur = -1;
+  for (int64_t l = 0; l < nT; l++) {
+    const int4 r = P.h_range[P.h_p2p_targets[l]];
+    const int n = r.w - r.z;
+    if (n > NF_ROWS) {
+      T.ltile[l] = (int32_t)T.nrow.size();
+      T.lrow0[l] = 0;
+      for (int k = 0; k < n; k += NF_ROWS) {
+        T.leaf.push_back(l);
+        T.leaf.push_back(l + 1);
+        T.nrow.push_back(std::min(NF_ROWS, n - k));
+      }
+      cur = -1;
+      continue;
+    }
+    if (cur < 0 || T.nrow[cur] + n > NF_ROWS) {
+      cur = (int64_t)T.nrow.size();
+      T.leaf.push_back(l);
+      T.leaf.push_back(l + 1);
+      T.nrow.push_back(0);
+    }
+    T.leaf[2 * cur + 1] = l + 1;
+    T.ltile[l] = (int32_t)cur;
+    T.lrow0[l] = T.nrow[cur];
+    T.nrow[cur] += n;
+  }
+  return T;
+}
+
+// the two-limb split precision; the three-limb one (24-bit operands) keeps the
+// FP32 CUDA-core near field, whose rounding is finer than a two-limb product's
+bool near_tc_wanted(const Plan& P) {
+  return P.opt.near_mode == 1 && P.opt.near_tc >= 0 && P.opt.precision == DEMAG_MIXED_BF16X3;
+}
+
 // Plan-time near field, in chunks of consecutive target leaves (at most
-// NEAR_KEYS_PER_CHUNK (target, source-node) candidates each) so that large
-// meshes never hold more than one chunk's keys and FP64 coefficients:
-//   pass 1 -- per chunk, the distinct source nodes (columns) of every target;
-//   pass 2 -- per chunk again, the columns written in place, the FP64
-//             coefficients integrated (k_near_build) and, on the mixed path,
-//             packed to the FP32 layout; only the FP64 path keeps W64.
+// NEAR_KEYS_PER_CHUNK (target, source-node) candidates each; with tiles, a
+// chunk ends only where a tile ends) so that large meshes never hold more than
+// one chunk's keys and FP64 coefficients:
+//   pass 1 -- per chunk, the distinct source nodes (columns) of every target
+//             leaf, and with tiles the distinct columns of every tile;
+//   pass 2 -- per chunk again, the columns, the FP64 coefficients integrated
+//             (k_near_build, fixed-point sums) and, on the mixed path, packed:
+//             to the FP32 per-leaf layout, or to the split-BF16 tiles of the
+//             tensor-core near field.  Only the FP64 path keeps W64.
 constexpr int64_t NEAR_KEYS_PER_CHUNK = int64_t(1) << 27;
 
 void build_near_field(Plan& P) {
   cudaStream_t s = P.stream;
-  const int64_t nT = (int64_t)P.h_p2p_targets.size();
   const bool mixed = P.opt.precision != DEMAG_FP64, dip = P.opt.sources == DEMAG_SOURCES_DIPOLES;
+  const bool patch = P.opt.sources == DEMAG_SOURCES_PATCHES;
+  const bool nodesrc = dip || patch;  // columns: the source leaves' own nodes
+  const bool tc = near_tc_wanted(P);
+  if (tc) {  // tiles follow the Morton order of the target nodes
+    std::stable_sort(P.h_p2p_targets.begin(), P.h_p2p_targets.end(),
+                     [&](int32_t a, int32_t b) { return P.h_range[a].z < P.h_range[b].z; });
+    DM_CUDA(cudaMemcpyAsync(P.p2p_targets, P.h_p2p_targets.data(), P.h_p2p_targets.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  }
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
   P.w_coloff = dalloc<int64_t>(P, nT + 1);
   P.w_off = dalloc<int64_t>(P, nT + 1);
   if (nT == 0) {
@@ -542,14 +748,20 @@ void build_near_field(Plan& P) {
     int64_t n = 0;
     for (int64_t e = P.h_p2p_off[T]; e < P.h_p2p_off[T + 1]; e++) {
       int4 r = P.h_range[P.h_p2p_src[e]];
-      n += dip ? (int64_t)(r.w - r.z) : 4ll * (r.y - r.x);
+      n += nodesrc ? (int64_t)(r.w - r.z) : 4ll * (r.y - r.x);
     }
     if (n > NEAR_KEYS_PER_CHUNK) fail(DEMAG_ERR_UNSUPPORTED, "near field of one target leaf too large");
     koff[ti + 1] = koff[ti] + n;
   }
+  NfTiles TL;
+  if (tc) TL = nf_make_tiles(P);
+  const int64_t ntiles = (int64_t)TL.nrow.size();
+  auto tile_of = [&](int64_t l) -> int64_t { return l < nT ? TL.ltile[l] : ntiles; };  // first tile of leaf l
   std::vector<int64_t> chunk{0};
-  for (int64_t ti = 0; ti < nT; ti++)
-    if (koff[ti + 1] - koff[chunk.back()] > NEAR_KEYS_PER_CHUNK) chunk.push_back(ti);
+  for (int64_t ti = 0; ti < nT; ti++) {
+    const bool may_cut = !tc || (TL.lrow0[ti] == 0 && (ti == 0 || TL.ltile[ti] != TL.ltile[ti - 1]));
+    if (ti > chunk.back() && may_cut && koff[ti + 1] - koff[chunk.back()] > NEAR_KEYS_PER_CHUNK) chunk.push_back(ti);
+  }
   chunk.push_back(nT);
   int64_t max_keys = 0;
   for (size_t c = 0; c + 1 < chunk.size(); c++) max_keys = std::max(max_keys, koff[chunk[c + 1]] - koff[chunk[c]]);
@@ -567,7 +779,7 @@ void build_near_field(Plan& P) {
     for (int64_t t = t0; t <= t1; t++) rel[t - t0] = koff[t] - koff[t0];
     DM_CUDA(cudaMemcpyAsync(dkoff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     k_near_keys<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
-                                                     P.tets_s, dkoff.p, dip, keys.p);
+                                                     P.tets_s, dkoff.p, nodesrc, keys.p);
     DM_LAUNCH("k_near_keys");
     size_t t = tb;
     DM_CUDA(cub::DeviceRadixSort::SortKeys(temp.p, t, keys.p, keys_s.p, (int)nk, 0, 64, s));
@@ -578,8 +790,47 @@ void build_near_field(Plan& P) {
     DM_CUDA(cudaStreamSynchronize(s));
     return hnu;
   };
-  // pass 1: column counts per target
-  std::vector<int64_t> hcol(nT + 1, 0);
+  // tiles: the distinct columns of the tiles [q0, q1) of the chunk, whose leaves'
+  // columns are in keys.p with chunk-relative offsets doff; returns the sorted
+  // keys (tile - q0) << 32 | node and their per-tile offsets (host)
+  auto tile_columns = [&](int64_t t0, int64_t q0, int64_t q1, const std::vector<int64_t>& lcnt,
+                          std::vector<int64_t>& toff) -> std::unique_ptr<Tmp<uint64_t>> {
+    std::vector<int64_t> tleaf(2 * (q1 - q0)), tkoff(q1 - q0 + 1, 0);
+    for (int64_t q = q0; q < q1; q++) {
+      tleaf[2 * (q - q0)] = TL.leaf[2 * q] - t0;
+      tleaf[2 * (q - q0) + 1] = TL.leaf[2 * q + 1] - t0;
+      int64_t n = 0;
+      for (int64_t l = TL.leaf[2 * q]; l < TL.leaf[2 * q + 1]; l++) n += lcnt[l - t0];
+      tkoff[q - q0 + 1] = tkoff[q - q0] + n;
+    }
+    const int64_t nk = tkoff[q1 - q0];
+    Tmp<int64_t> dtleaf(tleaf.size()), dtkoff(tkoff.size());
+    DM_CUDA(cudaMemcpyAsync(dtleaf.p, tleaf.data(), tleaf.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(dtkoff.p, tkoff.data(), tkoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    Tmp<uint64_t> tk(nk), tks(nk);
+    std::unique_ptr<Tmp<uint64_t>> tu(new Tmp<uint64_t>(nk));
+    k_nf_tile_keys<<<(unsigned)(q1 - q0), 128, 0, s>>>(dtleaf.p, dtkoff.p, doff.p, keys.p, tk.p);
+    DM_LAUNCH("k_nf_tile_keys");
+    size_t b1 = 0, b2 = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, b1, tk.p, tks.p, (int)nk, 0, 64, s);
+    cub::DeviceSelect::Unique(nullptr, b2, tks.p, tu->p, nu.p, (int)nk, s);
+    Tmp<char> tt(std::max(b1, b2));
+    DM_CUDA(cub::DeviceRadixSort::SortKeys(tt.p, b1, tk.p, tks.p, (int)nk, 0, 64, s));
+    DM_CUDA(cub::DeviceSelect::Unique(tt.p, b2, tks.p, tu->p, nu.p, (int)nk, s));
+    int hnu = 0;
+    DM_CUDA(cudaMemcpyAsync(&hnu, nu.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    Tmp<int64_t> dto(q1 - q0 + 1);
+    k_col_offsets<<<(unsigned)((std::max<int64_t>(hnu, q1 - q0 + 1) + 255) / 256), 256, 0, s>>>(tu->p, hnu, q1 - q0,
+                                                                                                 dto.p, nullptr);
+    DM_LAUNCH("k_col_offsets(tiles)");
+    toff.assign(q1 - q0 + 1, 0);
+    DM_CUDA(cudaMemcpyAsync(toff.data(), dto.p, toff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return tu;
+  };
+  // pass 1: column counts per target leaf (and per tile)
+  std::vector<int64_t> hcol(nT + 1, 0), tcol(ntiles, 0);
   for (size_t c = 0; c + 1 < chunk.size(); c++) {
     const int64_t t0 = chunk[c], t1 = chunk[c + 1];
     const int64_t nu_c = columns(t0, t1);
@@ -590,6 +841,13 @@ void build_near_field(Plan& P) {
     DM_CUDA(cudaMemcpyAsync(o.data(), doff.p, o.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
     for (int64_t t = t0; t < t1; t++) hcol[t + 1] = hcol[t0] + o[t - t0 + 1];
+    if (tc) {
+      std::vector<int64_t> lcnt(t1 - t0), toff;
+      for (int64_t t = t0; t < t1; t++) lcnt[t - t0] = o[t - t0 + 1] - o[t - t0];
+      const int64_t q0 = tile_of(t0), q1 = tile_of(t1);
+      tile_columns(t0, q0, q1, lcnt, toff);
+      for (int64_t q = q0; q < q1; q++) tcol[q] = toff[q - q0 + 1] - toff[q - q0];
+    }
   }
   const int64_t ncols = hcol[nT];
   if (ncols > (int64_t)INT32_MAX) fail(DEMAG_ERR_UNSUPPORTED, "near field too large for the precomputed mode");
@@ -601,51 +859,126 @@ void build_near_field(Plan& P) {
   }
   P.n_wcols = ncols;
   P.n_wentries = hw[nT];
-  P.w_cols = dalloc<int32_t>(P, std::max<int64_t>(ncols, 1));
+  // per-leaf columns: kept by the FP64 and FP32 layouts, per chunk only for the tiles
+  int64_t max_lcols = 0;
+  for (size_t c = 0; c + 1 < chunk.size(); c++) max_lcols = std::max(max_lcols, hcol[chunk[c + 1]] - hcol[chunk[c]]);
+  Tmp<int32_t> lcols_tmp(tc ? max_lcols : 0);
+  P.w_cols = dalloc<int32_t>(P, tc ? 1 : std::max<int64_t>(ncols, 1));
   DM_CUDA(cudaMemcpyAsync(P.w_coloff, hcol.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   DM_CUDA(cudaMemcpyAsync(P.w_off, hw.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  if (mixed) {
+  std::vector<int64_t> hcoff(ntiles + 1, 0), hwoff(ntiles + 1, 0);
+  std::vector<int32_t> hng(ntiles), hnpad(ntiles);
+  if (tc) {
+    // tile shapes, row nodes and the split-BF16 coefficient array
+    std::vector<int32_t> rown((size_t)std::max<int64_t>(ntiles, 1) * NF_ROWS, -1);
+    for (int64_t q = 0; q < ntiles; q++) {
+      hng[q] = (int32_t)((tcol[q] + 15) / 16);
+      hnpad[q] = (TL.nrow[q] + 15) / 16 * 16;
+      hcoff[q + 1] = hcoff[q] + 16ll * hng[q];
+      hwoff[q + 1] = hwoff[q] + 3ll * hng[q] * 64 * hnpad[q];
+    }
+    for (int64_t l = 0; l < nT; l++) {
+      const int4 r = P.h_range[P.h_p2p_targets[l]];
+      for (int i = 0; i < r.w - r.z; i++) {
+        const int rr = TL.lrow0[l] + i;
+        rown[(size_t)(TL.ltile[l] + rr / NF_ROWS) * NF_ROWS + rr % NF_ROWS] = r.z + i;
+      }
+    }
+    P.nf_ntiles = ntiles;
+    P.nf_ncols = hcoff[ntiles];
+    P.nf_wbytes = hwoff[ntiles];
+    P.nf_woff = dalloc<int64_t>(P, ntiles);
+    P.nf_coff = dalloc<int64_t>(P, ntiles);
+    P.nf_ng = dalloc<int32_t>(P, ntiles);
+    P.nf_npad = dalloc<int32_t>(P, ntiles);
+    P.nf_rownode = dalloc<int32_t>(P, rown.size());
+    P.nf_cols = dalloc<int32_t>(P, std::max<int64_t>(P.nf_ncols, 1));
+    P.nf_W = dalloc<unsigned char>(P, std::max<int64_t>(P.nf_wbytes, 16));
+    DM_CUDA(cudaMemcpyAsync(P.nf_woff, hwoff.data(), ntiles * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.nf_coff, hcoff.data(), ntiles * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.nf_ng, hng.data(), ntiles * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.nf_npad, hnpad.data(), ntiles * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(P.nf_rownode, rown.data(), rown.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemsetAsync(P.nf_W, 0, std::max<int64_t>(P.nf_wbytes, 16), s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  } else if (mixed) {
     P.w_off32 = dalloc<int64_t>(P, nT + 1);
     DM_CUDA(cudaMemcpyAsync(P.w_off32, hw32.data(), (nT + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     P.W32 = dalloc<float>(P, std::max<int64_t>(hw32[nT], 4));
-    P.W64 = nullptr;
-  } else {
-    P.W64 = dalloc<double>(P, std::max<int64_t>(hw[nT], 1));
   }
+  if (!mixed) P.W64 = dalloc<double>(P, std::max<int64_t>(hw[nT], 1));
   int64_t max_w = 0;
   for (size_t c = 0; c + 1 < chunk.size(); c++) max_w = std::max(max_w, hw[chunk[c + 1]] - hw[chunk[c]]);
   Tmp<double> wtmp(mixed ? max_w : 0);
-  // pass 2: columns in place, FP64 coefficients, FP32 copy
+  Tmp<int32_t> dltile(tc ? nT : 0), dlrow0(tc ? nT : 0);
+  if (tc) {
+    DM_CUDA(cudaMemcpyAsync(dltile.p, TL.ltile.data(), nT * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaMemcpyAsync(dlrow0.p, TL.lrow0.data(), nT * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  const double fix = ldexp(1.0, 60) / P.side;  // |W| <= sqrt(3) side, so every partial sum fits in 63 bits
+  // pass 2: columns, FP64 coefficients, FP32 or split-BF16 copy
   for (size_t c = 0; c + 1 < chunk.size(); c++) {
     const int64_t t0 = chunk[c], t1 = chunk[c + 1];
     const int64_t nu_c = columns(t0, t1);
+    // per-leaf column offsets (chunk-relative in doff) and columns
+    int32_t* lcols = tc ? lcols_tmp.p : P.w_cols + hcol[t0];
     k_col_offsets<<<(unsigned)((std::max<int64_t>(nu_c, t1 - t0 + 1) + 255) / 256), 256, 0, s>>>(
-        keys.p, nu_c, t1 - t0, doff.p, P.w_cols + hcol[t0]);
+        keys.p, nu_c, t1 - t0, doff.p, lcols);
     DM_LAUNCH("k_col_offsets");
+    std::vector<int64_t> rel(t1 - t0 + 1);
+    for (int64_t t = t0; t <= t1; t++) rel[t - t0] = hcol[t] - hcol[t0];
+    Tmp<int64_t> lcoloff(t1 - t0 + 1);
+    DM_CUDA(cudaMemcpyAsync(lcoloff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     double* W = P.W64;
     const int64_t* woff = P.w_off + t0;
+    Tmp<int64_t> wrel(t1 - t0 + 1);
     if (mixed) {  // chunk-relative offsets into the temporary FP64 block
-      std::vector<int64_t> rel(t1 - t0 + 1);
       for (int64_t t = t0; t <= t1; t++) rel[t - t0] = hw[t] - hw[t0];
-      DM_CUDA(cudaMemcpyAsync(doff.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      DM_CUDA(cudaMemcpyAsync(wrel.p, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
       W = wtmp.p;
-      woff = doff.p;
+      woff = wrel.p;
     }
-    DM_CUDA(cudaMemsetAsync(W + (mixed ? 0 : hw[t0]), 0, std::max<int64_t>(hw[t1] - hw[t0], 1) * sizeof(double), s));
+    const int64_t nw = std::max<int64_t>(hw[t1] - hw[t0], 1);
+    double* Wc = W + (mixed ? 0 : hw[t0]);
+    DM_CUDA(cudaMemsetAsync(Wc, 0, nw * sizeof(double), s));
     if (dip) {
       k_near_build_dipole<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off,
-                                                              P.p2p_src, P.nodes_s, P.node_vol_s, P.w_coloff + t0,
-                                                              P.w_cols, woff, W);
+                                                              P.p2p_src, P.nodes_s, P.node_vol_s, lcoloff.p, lcols,
+                                                              woff, W);
       DM_LAUNCH("k_near_build_dipole");
     } else {
-      k_near_build<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
-                                                       P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad, P.w_coloff + t0,
-                                                       P.w_cols, woff, W);
-      DM_LAUNCH("k_near_build");
+      if (patch) {
+        k_near_build_patch<<<(unsigned)(t1 - t0), 128, 0, s>>>(
+            P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad,
+            P.nt_off, P.nt_tet, lcoloff.p, lcols, woff, fix, (unsigned long long*)W);
+        DM_LAUNCH("k_near_build_patch");
+      } else {
+        k_near_build<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.p2p_off, P.p2p_src,
+                                                         P.nodes_s, P.tets_s, P.tet_geo, P.tet_grad, lcoloff.p,
+                                                         lcols, woff, fix, (unsigned long long*)W);
+        DM_LAUNCH("k_near_build");
+      }
+      k_fixed_to_double<<<1024, 256, 0, s>>>(nw, Wc, 1.0 / fix);
+      DM_LAUNCH("k_fixed_to_double");
     }
-    if (mixed) {
+    if (tc) {
+      std::vector<int64_t> lcnt(t1 - t0), toff;
+      for (int64_t t = t0; t < t1; t++) lcnt[t - t0] = hcol[t + 1] - hcol[t];
+      const int64_t q0 = tile_of(t0), q1 = tile_of(t1);
+      // the leaf columns of this chunk again in keys.p for the tile keys
+      std::unique_ptr<Tmp<uint64_t>> tu = tile_columns(t0, q0, q1, lcnt, toff);
+      Tmp<int64_t> dto(q1 - q0 + 1);
+      DM_CUDA(cudaMemcpyAsync(dto.p, toff.data(), toff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      k_nf_tile_cols<<<(unsigned)(q1 - q0), 128, 0, s>>>(tu->p, dto.p, P.nf_coff + q0, P.nf_cols);
+      DM_LAUNCH("k_nf_tile_cols");
+      k_nf_pack<<<(unsigned)(t1 - t0), 256, 0, s>>>(P.p2p_targets + t0, P.cell_range, lcoloff.p, lcols, woff, W,
+                                                    dltile.p + t0, dlrow0.p + t0, P.nf_woff, P.nf_coff, P.nf_ng,
+                                                    P.nf_npad, P.nf_cols, P.nf_W);
+      DM_LAUNCH("k_nf_pack");
+      DM_CUDA(cudaStreamSynchronize(s));
+    } else if (mixed) {
       // FP32 copy, [col][node][4] per target leaf (16-byte entries)
-      k_pack_w32<<<(unsigned)(t1 - t0), 256, 0, s>>>(P.p2p_targets + t0, P.cell_range, P.w_coloff + t0, woff,
+      k_pack_w32<<<(unsigned)(t1 - t0), 256, 0, s>>>(P.p2p_targets + t0, P.cell_range, lcoloff.p, woff,
                                                      P.w_off32 + t0, W, P.W32);
       DM_LAUNCH("k_pack_w32");
     }

@@ -13,14 +13,18 @@
 // on every device that loads libdemag.so, and keeps it until the process exits.
 // Its host-side name is only a stand-in for the device symbol, so its device
 // address is looked up once per device (cudaGetSymbolAddress, with that device
-// current) on the first call of the entry point on that device; that first
-// call should therefore come before any stream capture.
+// current) on the first call of the entry point on that device -- and again if
+// the device's context has changed since; that first call should therefore
+// come before any stream capture.  A bounded device wait that expires is
+// recorded in a flag inside the array; demag_eval_status reads it.
 //
 // Every call on a device uses the same array, and the array keeps the
 // contents of the previous call: each scratch buffer that must start at zero
 // is cleared on the stream by the call itself.  Calls that overlap on the GPU
 // (different streams, or a concurrent demag_eval_noalloc on another plan of the
 // same device) race on the array and must be serialised by the caller.
+#include <cuda.h>  // the CUcontext type; the driver entry point itself is fetched through the runtime
+
 #include <mutex>
 
 #include "common.cuh"
@@ -33,12 +37,39 @@ namespace {
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-unsigned char* g_addr[MAX_DEVICES] = {};  // device -> device address of g_noalloc_scratch
+struct ScratchAddr {
+  void* ctx = nullptr;         // the CUDA context the address belongs to
+  unsigned char* ptr = nullptr;
+};
+ScratchAddr g_addr[MAX_DEVICES];  // device -> device address of g_noalloc_scratch
 
+// the current CUDA context of the calling thread (nullptr if it cannot be told)
+void* current_context() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return (GetCurrent)f;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return (void*)c;
+}
+
+// Device address of the fixed array for the current device and context: looked
+// up once (cudaGetSymbolAddress with that device current) and kept; looked up
+// again when the thread's context of the device has changed (for instance after
+// cudaDeviceReset), or on every call if the context cannot be told.
 unsigned char* scratch_address(int device) {
   if (device < 0 || device >= MAX_DEVICES) fail(DEMAG_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_addr[device]) return g_addr[device];
+  if (g_addr[device].ptr && ctx && g_addr[device].ctx == ctx) return g_addr[device].ptr;
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
   if (e != cudaSuccess || ptr == nullptr) {
@@ -46,8 +77,8 @@ unsigned char* scratch_address(int device) {
     fail(DEMAG_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch area failed: ") +
                              cudaGetErrorString(e));
   }
-  g_addr[device] = (unsigned char*)ptr;
-  return g_addr[device];
+  g_addr[device] = ScratchAddr{ctx, (unsigned char*)ptr};
+  return g_addr[device].ptr;
 }
 
 // carve the buffers one evaluation of B states needs, 256-byte aligned
@@ -80,6 +111,8 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     w.u32 = c.take<float>(nn * B);
     const size_t qp = m2l_tc_pack_bytes(P, B);
     if (qp) w.QP = c.take<unsigned char>(qp);
+    const size_t mp = nf_mp_floats(P, B);
+    if (mp) w.MP = c.take<float>(mp);
   }
   if (!mixed || otf) w.u_s = c.take<double>(nn * B);
   if (otf) w.state = c.take<double>(nt * TET_STATE * B);
@@ -94,6 +127,7 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     W->L32 = w.L32;
     W->u32 = w.u32;
     W->QP = w.QP;
+    W->MP = w.MP;
     W->u_s = w.u_s;
     W->state = w.state;
     W->err = w.err;

@@ -467,6 +467,92 @@ __global__ void k_ghat_dipole(const int32_t* __restrict__ leaves, int64_t nleave
   (void)pm1;
 }
 
+// Vertex-patch sources (the paper's clustering, Sec. 2.1 "vertex interaction"
+// and Sec. 3.1-3.2): node i carries lambda_i M_i over every tet around it and
+// is binned by its own key.  A cell's source radius reaches the farthest vertex
+// of the tets around its nodes ("most remote directly connected vertex").
+__global__ void k_radii_patch(const int4* __restrict__ range, const double* __restrict__ centre,
+                              const double* __restrict__ nodes_s, const int32_t* __restrict__ tets_s,
+                              const int64_t* __restrict__ nt_off, const int32_t* __restrict__ nt_tet, double* rsrc) {
+  __shared__ unsigned long long s_src;
+  const int64_t c = blockIdx.x;
+  if (threadIdx.x == 0) s_src = 0ull;
+  __syncthreads();
+  const int4 r = range[c];
+  const double cx = centre[3 * c], cy = centre[3 * c + 1], cz = centre[3 * c + 2];
+  double ms = 0;
+  for (int64_t i = r.z + threadIdx.x; i < r.w; i += blockDim.x)
+    for (int64_t e = nt_off[i]; e < nt_off[i + 1]; e++)
+      for (int k = 0; k < 4; k++) {
+        const int64_t g = tets_s[4ll * nt_tet[e] + k];
+        ms = fmax(ms, dist_rn(nodes_s[3 * g], nodes_s[3 * g + 1], nodes_s[3 * g + 2], cx, cy, cz));
+      }
+  atomicMax(&s_src, (unsigned long long)__double_as_longlong(ms));
+  __syncthreads();
+  if (threadIdx.x == 0) rsrc[c] = __longlong_as_double((long long)s_src);
+}
+
+// Exact moment operator of vertex patches: for every own node i of a source
+// leaf and |m| <= p-1,
+//   Ghat[i][m] = sum_{t ni i} int_t lambda_i(r') y^m/m! dV,  y = r' - c_leaf,
+// with the Grundmann-Moeller rule of k_ghat.  One block per leaf, one thread
+// per multi-index m; supports are the leaf's own nodes in order.
+__global__ void k_ghat_patch(const int4* __restrict__ range, const int32_t* __restrict__ leaves, int64_t nleaves,
+                             const double* __restrict__ centre, const double* __restrict__ nodes_s,
+                             const int32_t* __restrict__ tets_s, const double* __restrict__ tet_vol,
+                             const int64_t* __restrict__ nt_off, const int32_t* __restrict__ nt_tet,
+                             const int64_t* __restrict__ sup_off, const double* __restrict__ gm, int ngm, int pm1,
+                             int nc1, double* Ghat) {
+  __shared__ double px[MAX_P + 1], py[MAX_P + 1], pz[MAX_P + 1];
+  __shared__ double lam_w[5];
+  const int64_t li = blockIdx.x;
+  if (li >= nleaves) return;
+  const int32_t c = leaves[li];
+  const int4 r = range[c];
+  const double cx = centre[3 * c], cy = centre[3 * c + 1], cz = centre[3 * c + 2];
+  const bool active = threadIdx.x < nc1;
+  int ma = 0, mb = 0, mc = 0;
+  if (active) mi_decode(threadIdx.x, ma, mb, mc);
+  for (int32_t i = r.z; i < r.w; i++) {
+    double gsum = 0.0;
+    for (int64_t e = nt_off[i]; e < nt_off[i + 1]; e++) {
+      const int32_t j = nt_tet[e];
+      double v[4][3];
+      int ki = 0;
+      for (int k = 0; k < 4; k++) {
+        const int64_t g = tets_s[4ll * j + k];
+        if (g == i) ki = k;
+        v[k][0] = nodes_s[3 * g];
+        v[k][1] = nodes_s[3 * g + 1];
+        v[k][2] = nodes_s[3 * g + 2];
+      }
+      double acc = 0.0;
+      for (int q = 0; q < ngm; q++) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const double l0 = gm[5 * q], l1 = gm[5 * q + 1], l2 = gm[5 * q + 2], l3 = gm[5 * q + 3];
+          double y[3];
+          for (int a = 0; a < 3; a++) y[a] = l0 * v[0][a] + l1 * v[1][a] + l2 * v[2][a] + l3 * v[3][a];
+          y[0] -= cx;
+          y[1] -= cy;
+          y[2] -= cz;
+          px[0] = py[0] = pz[0] = 1.0;
+          for (int d = 1; d <= pm1; d++) {
+            px[d] = px[d - 1] * y[0] / d;
+            py[d] = py[d - 1] * y[1] / d;
+            pz[d] = pz[d - 1] * y[2] / d;
+          }
+          for (int k = 0; k < 5; k++) lam_w[k] = gm[5 * q + k];
+        }
+        __syncthreads();
+        if (active) acc += lam_w[ki] * lam_w[4] * px[ma] * py[mb] * pz[mc];
+      }
+      gsum += tet_vol[j] * acc;
+    }
+    if (active) Ghat[(sup_off[c] + (i - r.z)) * nc1 + threadIdx.x] = gsum;
+  }
+}
+
 // Exact moment operator of a source leaf (Sec. 2.2, Eq. expCoeffs): for every
 // support node j of the leaf and |m| <= p-1,
 //   Ghat[j][m] = sum_{t in leaf, t ni j} int_t lambda_{k(t,j)}(r') y^m/m! dV,  y = r' - c_leaf,
@@ -756,6 +842,30 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   // orientation, per-tet geometry for the near field and for H (p2p.cu)
   build_tet_geometry(P);
 
+  // node -> incident tets (sorted by tet within a node): the lumped H, the vertex patches
+  {
+    Tmp<int32_t> key(4 * nt), val(4 * nt), key_s(4 * nt);
+    P.nt_off = dalloc<int64_t>(P, nn + 1);
+    P.nt_tet = dalloc<int32_t>(P, 4 * nt);
+    // keys = node ids in tets_s order; values = tet ids
+    DM_CUDA(cudaMemcpyAsync(key.p, P.tets_s, 4 * nt * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    std::vector<int32_t> hv(4 * nt);
+    for (int64_t q = 0; q < 4 * nt; q++) hv[q] = (int32_t)(q / 4);
+    DM_CUDA(cudaMemcpyAsync(val.p, hv.data(), 4 * nt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    size_t b = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, b, key.p, key_s.p, val.p, P.nt_tet, (int)(4 * nt), 0, 32, s);
+    ct.need(b);
+    DM_CUDA(cub::DeviceRadixSort::SortPairs(ct.p, b, key.p, key_s.p, val.p, P.nt_tet, (int)(4 * nt), 0, 32, s));
+    std::vector<int32_t> hk(4 * nt);
+    DM_CUDA(cudaMemcpyAsync(hk.data(), key_s.p, 4 * nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> off(nn + 1, 0);
+    for (int64_t q = 0; q < 4 * nt; q++) off[hk[q] + 1]++;
+    for (int64_t i = 0; i < nn; i++) off[i + 1] += off[i];
+    DM_CUDA(cudaMemcpyAsync(P.nt_off, off.data(), (nn + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
+
   // centres and radii (Sec. 3.2)
   P.cell_centre = dalloc<double>(P, 3 * nc);
   P.cell_rsrc = dalloc<double>(P, nc);
@@ -764,14 +874,20 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   DM_LAUNCH("k_centres");
   k_radii<<<(int)nc, 256, 0, s>>>(P.cell_range, P.cell_centre, P.nodes_s, P.tets_s, P.cell_rsrc, P.cell_rtgt);
   DM_LAUNCH("k_radii");
-  const bool dip = P.opt.sources == DEMAG_SOURCES_DIPOLES;
+  const bool dip = P.opt.sources == DEMAG_SOURCES_DIPOLES, patch = P.opt.sources == DEMAG_SOURCES_PATCHES;
+  const bool nodesrc = dip || patch;  // sources bound to the cells' own nodes
   if (dip)  // point dipoles at the cell's own nodes: the source radius is the node radius
     DM_CUDA(cudaMemcpyAsync(P.cell_rsrc, P.cell_rtgt, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (patch) {
+    k_radii_patch<<<(int)nc, 256, 0, s>>>(P.cell_range, P.cell_centre, P.nodes_s, P.tets_s, P.nt_off, P.nt_tet,
+                                          P.cell_rsrc);
+    DM_LAUNCH("k_radii_patch");
+  }
 
   // dual tree traversal (Sec. 3.3, Listings 1-2), breadth first
   {
     TravCells C{P.cell_range, P.cell_level, P.cell_child0, P.cell_nchild,
-                P.cell_centre, P.cell_rsrc, P.cell_rtgt, P.opt.theta, dip ? 1 : 0};
+                P.cell_centre, P.cell_rsrc, P.cell_rtgt, P.opt.theta, nodesrc ? 1 : 0};
     size_t cap_m = std::max<int64_t>(1024, 64 * nc), cap_p = std::max<int64_t>(1024, 32 * nc),
            cap_f = std::max<int64_t>(1024, 16 * nc);
     Tmp<uint64_t> m2l(cap_m), p2p(cap_p), cur(cap_f), nxt(cap_f);
@@ -870,11 +986,11 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
       int64_t ntg = h_range[c].w - h_range[c].z, nsrc = 0;
       for (int64_t e = h_p2p_off[c]; e < h_p2p_off[c + 1]; e++) {
         int4 r = h_range[h_p2p_src[e]];
-        nsrc += dip ? r.w - r.z : r.y - r.x;
+        nsrc += nodesrc ? r.w - r.z : r.y - r.x;
       }
       P.n_p2p_pairs += ntg * nsrc;
     }
-    if (leaf && (dip ? h_range[c].w > h_range[c].z : h_range[c].y > h_range[c].x))
+    if (leaf && (nodesrc ? h_range[c].w > h_range[c].z : h_range[c].y > h_range[c].x))
       P.h_src_leaves.push_back((int32_t)c);
   }
 
@@ -896,7 +1012,7 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
   DM_CUDA(cudaMemcpyAsync(P.src_leaves, P.h_src_leaves.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   P.sup_off = dalloc<int64_t>(P, nc + 1);
   P.tet_col = dalloc<int32_t>(P, 4 * nt);
-  if (dip) {  // a dipole leaf's support is its own nodes (sorted ids r.z .. r.w - 1)
+  if (nodesrc) {  // a dipole or patch leaf's support is its own nodes (sorted ids r.z .. r.w - 1)
     std::vector<int64_t> so(nc + 1, 0);
     std::vector<int32_t> sn;
     std::vector<char> is_src(nc, 0);
@@ -958,34 +1074,17 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     P.Ghat = dalloc<double>(P, std::max<int64_t>(P.n_sup, 1) * P.nc1);
     DM_CUDA(cudaMemsetAsync(P.Ghat, 0, std::max<int64_t>(P.n_sup, 1) * P.nc1 * sizeof(double), s));
     int threads = ((P.nc1 + 31) / 32) * 32;
-    k_ghat<<<(int)std::max<int64_t>(nsl, 1), threads, 0, s>>>(P.cell_range, P.src_leaves, nsl, P.cell_centre,
-                                                                P.nodes_s, P.tets_s, P.tet_vol, P.sup_off, P.tet_col,
-                                                                dgm.p, ngm, pm1, P.nc1, P.Ghat);
-    DM_LAUNCH("k_ghat");
-    DM_CUDA(cudaStreamSynchronize(s));
-  }
-
-  // node -> incident tets (sorted by tet within a node), for the lumped H
-  {
-    Tmp<int32_t> key(4 * nt), val(4 * nt), key_s(4 * nt);
-    P.nt_off = dalloc<int64_t>(P, nn + 1);
-    P.nt_tet = dalloc<int32_t>(P, 4 * nt);
-    // keys = node ids in tets_s order; values = tet ids
-    DM_CUDA(cudaMemcpyAsync(key.p, P.tets_s, 4 * nt * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    std::vector<int32_t> hv(4 * nt);
-    for (int64_t q = 0; q < 4 * nt; q++) hv[q] = (int32_t)(q / 4);
-    DM_CUDA(cudaMemcpyAsync(val.p, hv.data(), 4 * nt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    size_t b = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, b, key.p, key_s.p, val.p, P.nt_tet, (int)(4 * nt), 0, 32, s);
-    ct.need(b);
-    DM_CUDA(cub::DeviceRadixSort::SortPairs(ct.p, b, key.p, key_s.p, val.p, P.nt_tet, (int)(4 * nt), 0, 32, s));
-    std::vector<int32_t> hk(4 * nt);
-    DM_CUDA(cudaMemcpyAsync(hk.data(), key_s.p, 4 * nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DM_CUDA(cudaStreamSynchronize(s));
-    std::vector<int64_t> off(nn + 1, 0);
-    for (int64_t q = 0; q < 4 * nt; q++) off[hk[q] + 1]++;
-    for (int64_t i = 0; i < nn; i++) off[i + 1] += off[i];
-    DM_CUDA(cudaMemcpyAsync(P.nt_off, off.data(), (nn + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (patch) {
+      k_ghat_patch<<<(int)std::max<int64_t>(nsl, 1), threads, 0, s>>>(
+          P.cell_range, P.src_leaves, nsl, P.cell_centre, P.nodes_s, P.tets_s, P.tet_vol, P.nt_off, P.nt_tet,
+          P.sup_off, dgm.p, ngm, pm1, P.nc1, P.Ghat);
+      DM_LAUNCH("k_ghat_patch");
+    } else {
+      k_ghat<<<(int)std::max<int64_t>(nsl, 1), threads, 0, s>>>(P.cell_range, P.src_leaves, nsl, P.cell_centre,
+                                                                  P.nodes_s, P.tets_s, P.tet_vol, P.sup_off,
+                                                                  P.tet_col, dgm.p, ngm, pm1, P.nc1, P.Ghat);
+      DM_LAUNCH("k_ghat");
+    }
     DM_CUDA(cudaStreamSynchronize(s));
   }
 

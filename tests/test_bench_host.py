@@ -36,7 +36,7 @@ def test_m2l_counts():
 def test_roofline_record_tensor_and_alu():
     stats = {"stage_ms": {"m2l": 80.0, "p2p": 30.0}, "stage_launches": {"m2l": 10, "p2p": 10}, "_batch": 128,
              "p": 8, "n_m2l": 866523, "near_mode": 1, "n_near_cols": 107e6, "leaf_size": 128, "n_tets": 223668,
-             "m2l_targets_per_cta": 1, "m2l_kps": 2}
+             "n_nodes": 35840, "m2l_targets_per_cta": 1, "m2l_kps": 2}
     peaks = {"bf16_tflops_sustained": 1744.5, "hbm_gbs": 6689.8}
     r = bench.roofline_for(stats, 10, "bf16x3", peaks, 2070.0, tensor_m2l=True)
     assert r["kernel"] == "m2l" and r["bound"] == "tensor" and r["peak"] == 1744.5
@@ -44,3 +44,30 @@ def test_roofline_record_tensor_and_alu():
     assert abs(r["achieved"] - achieved) < 1e-9 * achieved and abs(r["frac"] - achieved / 1744.5) < 1e-12
     r2 = bench.roofline_for(stats, 10, "bf16x3", peaks, 2070.0, tensor_m2l=False)
     assert r2["bound"] == "alu" and abs(r2["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+
+
+def test_roofline_near_field_record():
+    """The stored near field on the tensor cores is held against HBM: 12 B of
+    split-BF16 coefficients per (target, source node) pair, M and u of every
+    node once per state; its tensor-pipe view counts 2 flops per component."""
+    stats = {"stage_ms": {"m2l": 10.0, "p2p": 30.0}, "stage_launches": {"m2l": 10, "p2p": 10}, "_batch": 256,
+             "p": 8, "n_m2l": 1000, "near_mode": 1, "n_near_cols": 583e6, "n_near_tiles": 700, "near_bytes": 10e9,
+             "leaf_size": 512, "n_tets": 559564, "n_nodes": 87443}
+    peaks = {"bf16_tflops_sustained": 1705.4, "hbm_gbs": 6766.0}
+    r = bench.roofline_for(stats, 10, "bf16x3", peaks, 2070.0)
+    assert r["kernel"] == "p2p" and r["bound"] == "hbm" and r["peak"] == 6766.0
+    alg = 583e6 * 12 + 87443 * 256 * 12 + 87443 * 256 * 8
+    assert abs(r["algorithmic_bytes"] - alg) < 1e-9 * alg
+    assert abs(r["achieved"] - alg / 3e-3 / 1e9) < 1e-9 * r["achieved"]
+    tv = r["tensor_view"]
+    assert abs(tv["achieved"] - 2.0 * 3 * 583e6 * 256 / 3e-3 / 1e12) < 1e-9 * tv["achieved"]
+    assert r["stages"]["m2l"]["bound"] == "tensor" and r["stages"]["p2p"]["bound"] == "hbm"
+
+
+def test_workload_defaults_fill_batch_and_autotune():
+    a = types.SimpleNamespace(workload="sphere500k", p=0, leaf=0, theta=0.0, batch=0, autotune=-1)
+    w = bench.workload(a)
+    assert a.batch == 256 and a.autotune == 3 and w["cpu_leaf"] == 128
+    b = types.SimpleNamespace(workload="sphere500k", p=0, leaf=512, theta=0.0, batch=0, autotune=-1)
+    w = bench.workload(b)
+    assert b.autotune == 1 and w["leaf"] == 512 and w["cpu_leaf"] == 512  # a given leaf is not tuned

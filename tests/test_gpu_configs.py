@@ -151,8 +151,11 @@ def test_graded_20m(orc):
     p64.close()
     del p64
     torch.cuda.empty_cache()
+    # the per-leaf FP32 near field (near_tc = -1): with ~2 target nodes per 64-tet leaf a
+    # 128-node tile spans ~60 leaves, whose column union would store the coefficients
+    # several times over and leave no room for the batch within 180 GB
     pl = Plan(nodes, tets, p=8, leaf_size=64, theta=0.5, precision="bf16x3", near_mode=1, max_batch=32,
-              m2l_table_batch=32)
+              m2l_table_batch=32, near_tc=-1)
     st = pl.stats()
     # the batch: the largest power of two (at most 32) whose workspace and inputs/outputs fit in
     # 180 GB with the plan (FP32 moments and locals per cell, FP32 and FP64 node arrays per state)

@@ -92,3 +92,29 @@ def test_llg_batch_steps_like_single_states():
     for k in range(2):
         pl.llg_rk4(ms[k], Ms=1.0, alpha=0.2, h_ext=(0.0, 0.0, 0.1), dt=0.02, steps=5)
         assert float(torch.max(torch.abs(ms[k][0] - m[k]))) < 1e-12
+
+
+def test_energy_and_llg_rk4_against_the_oracle(orc):
+    """demag_energy and demag_llg_rk4 (FP64 path) against the oracle's energy and
+    RK4 stepping, whose field at every stage is the oracle's own FMM (same tree
+    rules, p, leaf and theta) followed by its mass-lumped H: the library's FP64
+    FMM agrees with the oracle FMM to rounding, so three steps agree to 1e-9."""
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=0.2)
+    B, p, leaf, theta = 2, 6, 32, 0.5
+    m0 = inputs.smoothed_unit_m(tets, nodes.shape[0], batch=B, seed=43)
+    Ms, alpha, hext, dt, steps = 1.0, 0.2, (0.1, 0.0, 0.3), 0.05, 3
+    pl = Plan(nodes, tets, p=p, leaf_size=leaf, theta=theta, near_mode=1, max_batch=B)
+    md = torch.as_tensor(m0, device="cuda")
+    u, H = pl.eval(md)
+    e = pl.energy(md, H).cpu().numpy()
+    tree = orc.Tree(nodes, tets, leaf, theta)
+    Hor = orc.lumped_H(nodes, tets, tree.fmm(m0, p))
+    assert np.abs(e - orc.energy(nodes, tets, m0, H.cpu().numpy())).max() <= 1e-13 * np.abs(e).max()
+    assert np.abs(e - orc.energy(nodes, tets, m0, Hor)).max() <= 1e-10 * np.abs(e).max()
+    pl.llg_rk4(md, Ms=Ms, alpha=alpha, h_ext=hext, dt=dt, steps=steps)
+    torch.cuda.synchronize()
+    field = lambda M: orc.lumped_H(nodes, tets, tree.fmm(M, p))
+    mor = orc.llg_rk4(m0, field, Ms, alpha, hext, dt, steps)
+    assert np.abs(md.cpu().numpy() - mor).max() < 1e-9

@@ -111,13 +111,15 @@ def test_table_m2l_vs_fp64(p, B):
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_small_batch_tensor_precisions_use_the_table_m2l(prec):
     """At batches up to m2l_table_batch (default 8) the tensor-core precisions
-    run the same FP32 kernels as the FP32 precision: identical bits."""
+    run the same FP32 M2L kernels as the FP32 precision: identical bits when the
+    near field runs on CUDA cores too (near_tc = -1; TF32 always does)."""
     nodes, tets = inputs.sphere(h=0.13)
     M = inputs.gaussian_unit_m(nodes.shape[0], batch=4, seed=91)
     a = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision="fp32").eval(M)
-    b = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec).eval(M)
+    b = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec, near_tc=-1).eval(M)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
-    c = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec, m2l_table_batch=-1).eval(M)
+    c = _plan(nodes, tets, p=8, leaf_size=32, max_batch=4, near_mode=1, precision=prec, m2l_table_batch=-1,
+              near_tc=-1).eval(M)
     assert not torch.equal(a[0], c[0])  # forced onto the tensor cores
 
 

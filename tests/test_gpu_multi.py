@@ -63,3 +63,27 @@ def test_multi_rejects_bad_arguments():
         eval_multi_into([pl], [M3], [torch.empty((3, nodes.shape[0]), dtype=torch.float64, device="cuda")])
     with pytest.raises(RuntimeError):  # host pointers
         eval_multi_into([pl], [M.cpu()], [u])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_single_eval_graph_replay(prec):
+    """graph = 1: demag_eval with device pointers records its first call as a
+    CUDA graph and replays it; results equal a plan without graphs, bit for
+    bit, on the first call and on replays with new values in the same
+    tensors."""
+    from paper_1606_00247_gb300.api import Plan
+
+    nodes, tets = inputs.sphere(h=0.15)
+    B = 8 if prec == "fp64" else 128
+    kw = dict(p=6, leaf_size=32, near_mode=1, max_batch=B, precision=prec)
+    g = Plan(nodes, tets, graph=True, **kw)
+    d = Plan(nodes, tets, **kw)
+    M = torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], batch=B, seed=61), device="cuda")
+    u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device="cuda")
+    H = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64, device="cuda")
+    for seed in (61, 62, 63):
+        M.copy_(torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], batch=B, seed=seed)))
+        g.eval(M, u, H)
+        ud, Hd = d.eval(M)
+        torch.cuda.synchronize()
+        assert torch.equal(u, ud) and torch.equal(H, Hd), seed
