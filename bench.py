@@ -469,6 +469,9 @@ def run_ours(args, rank, world, local_rank):
     total_ms = float(sum(step_ms))
     launches = plan.stats()["eval_launches"] * args.steps
     u_acc, H_acc = u.clone(), H.clone()  # the timed evaluation's outputs, for the accuracy gate
+    from paper_1606_00247_gb300 import _lib as L
+
+    device_status = L.demag_status_string(L.demag_eval_status(plan.handle, stream.cuda_stream))
     total_ms, value = aggregate_ranks(total_ms, B * args.steps, world, dev)
 
     # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside)
@@ -492,6 +495,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(nprof):
         flush.zero_()
         prof.eval(M, u, H)
+    prof_status = L.demag_status_string(L.demag_eval_status(prof.handle, stream.cuda_stream))
     pst = prof.stats()
     pst["_batch"] = B
     pst["near_mode"] = args.near_mode
@@ -565,6 +569,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
+        "device_status": {"timed": device_status, "profiled": prof_status},
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nodes, tets, w, make_M(nodes.shape[0], 1, tets=tets, w=w)[0],

@@ -180,6 +180,7 @@ struct Plan {
   int32_t* nf_npad = nullptr;       // ntiles: rows padded to 16
   int32_t* nf_rownode = nullptr;    // ntiles x NF_ROWS: sorted node of each row, -1 = none
   int32_t* nf_cols = nullptr;       // sorted node of each column (groups padded with the last column)
+  int32_t* nf_order = nullptr;      // ntiles: launch order, by decreasing column groups
   unsigned char* nf_W = nullptr;
 
   // tensor-core M2L (TF32 / split BF16): one operator tile set per distinct

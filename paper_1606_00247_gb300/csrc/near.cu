@@ -894,6 +894,11 @@ void build_near_field(Plan& P) {
     P.nf_rownode = dalloc<int32_t>(P, rown.size());
     P.nf_cols = dalloc<int32_t>(P, std::max<int64_t>(P.nf_ncols, 1));
     P.nf_W = dalloc<unsigned char>(P, std::max<int64_t>(P.nf_wbytes, 16));
+    std::vector<int32_t> order(ntiles);
+    for (int64_t q = 0; q < ntiles; q++) order[q] = (int32_t)q;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return hng[a] > hng[b]; });
+    P.nf_order = dalloc<int32_t>(P, std::max<int64_t>(ntiles, 1));
+    DM_CUDA(cudaMemcpyAsync(P.nf_order, order.data(), ntiles * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     DM_CUDA(cudaMemcpyAsync(P.nf_woff, hwoff.data(), ntiles * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     DM_CUDA(cudaMemcpyAsync(P.nf_coff, hcoff.data(), ntiles * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     DM_CUDA(cudaMemcpyAsync(P.nf_ng, hng.data(), ntiles * sizeof(int32_t), cudaMemcpyHostToDevice, s));

@@ -87,7 +87,8 @@ __global__ void k_nf_pack_m(int64_t nn, int B, const float* __restrict__ Ms, flo
 // state warps add each finished chunk into FP32 totals in shared memory
 // (round to nearest) while the other accumulator fills.
 __global__ void __launch_bounds__(NF_THREADS, 1)
-    k_near_tc(const int64_t* __restrict__ woff, const int64_t* __restrict__ coff, const int32_t* __restrict__ ngrp,
+    k_near_tc(const int32_t* __restrict__ order, const int64_t* __restrict__ woff, const int64_t* __restrict__ coff,
+              const int32_t* __restrict__ ngrp,
               const int32_t* __restrict__ npad_t, const int32_t* __restrict__ rownode,
               const int32_t* __restrict__ cols, const unsigned char* __restrict__ W, const float* __restrict__ MP,
               int64_t nn, int B, float* u, int* err, int debug_no_copies) {
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
   int* counts = (int*)(tmem_slot + 2);  // stages issued, stages consumed by the MMA issuer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sb = blockIdx.x;
-  const int64_t tile = blockIdx.y;
+  const int64_t tile = order ? order[blockIdx.y] : blockIdx.y;
   const int ng = ngrp[tile];
   if (ng == 0) return;  // uniform over the CTA
   const int npad = npad_t[tile];
@@ -144,8 +145,11 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     const unsigned char* Wt = W + woff[tile];
     const float* MPb = MP + (int64_t)sb * nn * 384;
     int g = 0;
+    int col_next = lane < 16 ? ct[lane] : 0;  // column ids one group ahead
     if (!debug_no_copies) {  // test hook: no stage is ever filled, so the waits for them expire
       for (; g < ng; g++) {
+        const int col = col_next;
+        if (g + 1 < ng && lane < 16) col_next = ct[16 * (g + 1) + lane];
         const int slot = g % NF_STAGES;
         int ok = 1;
         if (g >= NF_STAGES) {
@@ -160,7 +164,6 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
           break;
         }
         if (*abort_flag) break;
-        const int col = lane < 16 ? ct[16 * g + lane] : 0;
         const uint32_t dst = ring0 + (uint32_t)slot * NF_STAGE;
         if (lane == 0) expect_tx(sfull(slot), 3u * kbytes + 16u * NF_MCOL);
         __syncwarp();
@@ -173,40 +176,56 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     if (lane == 0) counts[0] = g;
     __syncwarp();
   } else if (warp == 1) {
-    if (lane == 0) {  // ---- MMA issuer
+    if (lane == 0) {  // ---- MMA issuer: running ring positions, no divisions in the loop
       const uint32_t id = idesc_bf16(128, npad);
-      int consumed = 0;
+      const uint64_t dstep = (uint64_t)(kbytes >> 4);  // descriptor start-address step of one k-step
+      const uint64_t dlimb = (uint64_t)((32u * (uint32_t)npad) >> 4);
+      uint32_t sslot = 0, sphase = 0, aslot = 0, aphase = 0, db = 0;
+      int kc = 0, c = 0, consumed = 0;
       bool bad = false;
-      for (int ks = 0; ks < nk && !bad; ks++) {
-        const int st = ks / 3, j = ks - 3 * st, slot = st % NF_STAGES, aslot = ks % NF_RING;
-        const int c = ks / NF_CHUNK, db = c & 1, kc = ks - c * NF_CHUNK;
-        if (kc == 0 && c >= 2 && !mbar_wait(dfree(db), (uint32_t)((c / 2 - 1) & 1), abort_flag)) {
-          bad = true;  // the state warps have not read the chunk that last used this accumulator
-          break;
-        }
-        if (j == 0) {
-          if (!mbar_wait(sfull(slot), (uint32_t)((st / NF_STAGES) & 1), abort_flag)) {
-            bad = true;
-            break;
-          }
-          consumed = st + 1;
-        }
-        if (!mbar_wait(afull(aslot), (uint32_t)((ks / NF_RING) & 1), abort_flag)) {
+      for (int g = 0; g < ng && !bad; g++) {
+        if (!mbar_wait(sfull(sslot), sphase, abort_flag)) {
           bad = true;
           break;
         }
-        fence_after();
-        const uint32_t bb = ring0 + (uint32_t)slot * NF_STAGE + (uint32_t)j * kbytes;
-        const uint64_t bhi = sdesc(bb), blo = sdesc(bb + 32u * (uint32_t)npad);
-        const uint32_t a = tmem + NF_RING0 + aslot * 16;
-        const uint32_t d = tmem + 128 * db;
-        mma_ts_bf16(d, a, bhi, id, kc > 0 ? 1u : 0u);
-        mma_ts_bf16(d, a, blo, id, 1u);
-        mma_ts_bf16(d, a + 8, bhi, id, 1u);
-        mma_commit(aempty(aslot));                                      // the A slot is free once these are done
-        if (j == 2) mma_commit(sempty(slot));                           // the stage's W after its last k-step
-        if (kc == NF_CHUNK - 1 || ks == nk - 1) mma_commit(dfull(db));  // the chunk is complete
+        consumed = g + 1;
+        uint64_t bhi = sdesc(ring0 + sslot * NF_STAGE);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          if (kc == 0 && c >= 2 && !mbar_wait(dfree(db), (uint32_t)((c / 2 - 1) & 1), abort_flag)) {
+            bad = true;  // the state warps have not read the chunk that last used this accumulator
+            break;
+          }
+          if (!mbar_wait(afull(aslot), aphase, abort_flag)) {
+            bad = true;
+            break;
+          }
+          fence_after();
+          const uint32_t a = tmem + NF_RING0 + aslot * 16, d = tmem + 128 * db;
+          mma_ts_bf16(d, a, bhi, id, kc > 0 ? 1u : 0u);
+          mma_ts_bf16(d, a, bhi + dlimb, id, 1u);
+          mma_ts_bf16(d, a + 8, bhi, id, 1u);
+          mma_commit(aempty(aslot));  // the A slot is free once these are done
+          bhi += dstep;
+          if (++aslot == NF_RING) {
+            aslot = 0;
+            aphase ^= 1u;
+          }
+          if (++kc == NF_CHUNK) {  // the chunk is complete
+            mma_commit(dfull(db));
+            kc = 0;
+            db ^= 1u;
+            c++;
+          }
+        }
+        if (bad) break;
+        mma_commit(sempty(sslot));  // the stage's W after its last k-step
+        if (++sslot == NF_STAGES) {
+          sslot = 0;
+          sphase ^= 1u;
+        }
       }
+      if (!bad && kc > 0) mma_commit(dfull(db));  // the last, partial chunk
       if (bad) {
         if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
         *abort_flag = 1;
@@ -232,7 +251,8 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       if (lane == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
       return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
-    // add this warp's rows of accumulator chunk c into the totals
+    // add this warp's rows (16-row chunks 2 i + h) of accumulator chunk c into
+    // the FP32 totals (round to nearest)
     auto promote = [&](int c) {
       if (!wait_warp(dfull(c & 1), (uint32_t)((c / 2) & 1))) {
         bad = true;
@@ -250,41 +270,47 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       if (lane == 0) mbar_arrive(dfree(c & 1));
       promoted = c + 1;
     };
+    // one hand-off per column group: its three k-steps (x, y, z) fill three
+    // consecutive A slots; the MMAs complete in order, so the slot of the
+    // group's last k-step being free means the other two are free as well
     for (int g = h; g < ng && !bad; g += 2) {
-      const int slot = g % NF_STAGES;
+      const int slot = g % NF_STAGES, ks0 = 3 * g;
       if (!wait_warp(sfull(slot), (uint32_t)((g / NF_STAGES) & 1))) {
         bad = true;
         break;
       }
       const float* mst = (const float*)(sm + (size_t)slot * NF_STAGE + NF_WPART);  // [column][c][128]
+      float v[3][16];
+#pragma unroll
+      for (int k = 0; k < 16; k++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) v[cc][k] = mst[(k * 3 + cc) * 128 + bl];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sempty(slot));  // this warp has read the stage's M
+      const int kl = ks0 + 2;
+      if (kl >= NF_RING && !wait_warp(aempty(kl % NF_RING), (uint32_t)((kl / NF_RING - 1) & 1))) {
+        bad = true;  // the MMAs of k-step kl - NF_RING have not read its slot
+        break;
+      }
+      fence_after();
 #pragma unroll
       for (int cc = 0; cc < 3; cc++) {
-        const int ks = 3 * g + cc, aslot = ks % NF_RING;
-        float v[16];
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = mst[(k * 3 + cc) * 128 + bl];
-        if (ks >= NF_RING && !wait_warp(aempty(aslot), (uint32_t)((ks / NF_RING - 1) & 1))) {
-          bad = true;  // the MMAs of k-step ks - NF_RING have not read this slot
-          break;
-        }
-        fence_after();
         uint32_t hi[8], lo[8];
-        split_bf16x16(v, hi, lo);
-        const uint32_t a = tmem + lane_off + NF_RING0 + aslot * 16;
+        split_bf16x16(v[cc], hi, lo);
+        const uint32_t a = tmem + lane_off + NF_RING0 + ((ks0 + cc) % NF_RING) * 16;
         tmem_st8(a, hi);
         tmem_st8(a + 8, lo);
-        tmem_wait_st();
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(afull(aslot));
-        // the earlier accumulator chunks, once this one is well under way
-        const int c = ks / NF_CHUNK;
-        if (ks - c * NF_CHUNK >= NF_PROMOTE_AT)
-          while (!bad && promoted < c) promote(promoted);
-        if (bad) break;
       }
+      tmem_wait_st();
+      fence_before();
       __syncwarp();
-      if (!bad && lane == 0) mbar_arrive(sempty(slot));  // this warp has read the stage's M
+      if (lane == 0)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) mbar_arrive(afull((ks0 + cc) % NF_RING));
+      // the earlier accumulator chunks, once this one is well under way
+      const int c = kl / NF_CHUNK;
+      if (kl - c * NF_CHUNK >= NF_PROMOTE_AT)
+        while (!bad && promoted < c) promote(promoted);
     }
     while (!bad && promoted < nch) promote(promoted);
     if (bad && lane == 0) {
@@ -332,7 +358,15 @@ void launch_near_tc(Plan& P, const float* Ms, float* MP, int B, float* u_s, int*
   k_nf_pack_m<<<dim3((unsigned)P.nn, nsb), 128, 0, s>>>(P.nn, B, Ms, MP);
   DM_LAUNCH("k_nf_pack_m");
   const dim3 grid(nsb, (unsigned)P.nf_ntiles);
-  k_near_tc<<<grid, NF_THREADS, NF_SMEM, s>>>(P.nf_woff, P.nf_coff, P.nf_ng, P.nf_npad, P.nf_rownode, P.nf_cols,
+  // launch order: a grid of a few waves starts its largest tiles first (a short
+  // tail); a long one runs in Morton order, so that the CTAs in flight gather
+  // the M of neighbouring columns from L2 (on GB300 the first is faster on the
+  // 224k-tet ball at 128 states, ~2 waves; the second on the 559k-tet ball at
+  // 256 states, ~10 waves)
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device);
+  const int32_t* order = (int64_t)grid.x * grid.y < 4ll * nsm ? P.nf_order : nullptr;
+  k_near_tc<<<grid, NF_THREADS, NF_SMEM, s>>>(order, P.nf_woff, P.nf_coff, P.nf_ng, P.nf_npad, P.nf_rownode, P.nf_cols,
                                               P.nf_W, MP, P.nn, B, u_s, err, P.debug_flags & 1);
   DM_LAUNCH("k_near_tc");
 }

@@ -37,11 +37,14 @@ static __device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity) 
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity to complete: one try_wait
-// (which may suspend the thread for a short, hardware-defined time), then at
-// most 2^24 non-blocking polls 64 ns apart (~1.5 s); gives up early as soon
-// as *abort_flag is set by another role.
+// (which may suspend the thread for a short, hardware-defined time), 512
+// non-blocking polls back to back (hand-offs inside a pipeline are short),
+// then at most 2^24 polls 64 ns apart (~1.5 s); gives up early as soon as
+// *abort_flag is set by another role.
 static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_test(bar, parity)) return true;
+  for (int it = 0; it < 512; it++)
+    if (mbar_poll(bar, parity)) return true;
   for (int it = 0; it < (1 << 24); it++) {
     if (mbar_poll(bar, parity)) return true;
     if (abort_flag && *abort_flag) return false;
