@@ -69,6 +69,8 @@ def lib():
             L.oracle_direct.argtypes = [vp, i64, vp, i64, vp, i32, vp, i64, vp, i32]
             L.oracle_direct_charges.restype = i32
             L.oracle_direct_charges.argtypes = [vp, i64, vp, i64, vp, i64, vp, i32, vp, i64, vp, i32]
+            L.oracle_field_charges.restype = i32
+            L.oracle_field_charges.argtypes = [vp, i64, vp, i64, vp, i64, vp, i32, vp, i64, vp, i32]
             L.oracle_lumped_H.restype = i32
             L.oracle_lumped_H.argtypes = [vp, i64, vp, i64, vp, i32, vp]
             L.oracle_tet_volumes.restype = None
@@ -191,6 +193,38 @@ def direct_charges(nodes, tets, M, targets=None, nthreads=0):
     if rc:
         raise RuntimeError("oracle_direct_charges failed")
     return u[0] if squeeze else u
+
+
+def field_charges(nodes, tets, M, points, nthreads=0):
+    """Pointwise field H = -grad u (B, n_pts, 3) at points (n_pts, 3) that lie on
+    no boundary face, by the whole-mesh charge route in closed form: the field
+    of the boundary faces' affine surface charges n.M plus every tet's constant
+    volume charge -div M (the remark of Sec. 4.1-4.2 on computing H directly)."""
+    nodes, tets = _f64(nodes), _i32(tets)
+    M = _f64(M)
+    squeeze = M.ndim == 2
+    if squeeze:
+        M = M[None]
+    B = M.shape[0]
+    pts = _f64(points).reshape(-1, 3)
+    bf = np.ascontiguousarray(boundary_faces(tets))
+    H = np.zeros((B, pts.shape[0], 3))
+    rc = lib().oracle_field_charges(_p(nodes), nodes.shape[0], _p(tets), tets.shape[0], _p(bf), bf.shape[0], _p(M), B,
+                                    _p(pts), pts.shape[0], _p(H), nthreads)
+    if rc:
+        raise RuntimeError("oracle_field_charges failed")
+    return H[0] if squeeze else H
+
+
+def interior_nodes(tets, n_nodes):
+    """Indices of the nodes that lie on no boundary face (where the pointwise field is defined)."""
+    t = np.asarray(tets, dtype=np.int64)
+    bf = boundary_faces(t)
+    on = np.zeros(n_nodes, bool)
+    for f in range(4):
+        sel = bf[bf[:, 1] == f, 0]
+        on[np.delete(t[sel], f, axis=1).ravel()] = True
+    return np.where(~on)[0]
 
 
 def lumped_volumes(nodes, tets):

@@ -61,6 +61,11 @@ int oracle_lumped_H(const double* nodes, int64_t n_nodes, const int32_t* tets, i
 int oracle_direct_charges(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                           const int32_t* bfaces, int64_t n_bfaces, const double* M, int B,
                           const int64_t* targets, int64_t n_targets, double* u, int nthreads);
+/* Pointwise H = -grad u at points off the boundary faces (whole-mesh charge
+ * route, closed forms): H is B x n_pts x 3. */
+int oracle_field_charges(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const int32_t* bfaces, int64_t n_bfaces, const double* M, int B, const double* pts,
+                         int64_t n_pts, double* H, int nthreads);
 void oracle_tet_volumes(const double* nodes, const int32_t* tets, int64_t n_tets, double* vol);
 
 /* ---- expansions (Sec. 2.2-2.3) -------------------------------------------- */

@@ -537,6 +537,155 @@ int oracle_direct_charges(const double* nodes, int64_t n_nodes, const int32_t* t
   return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * Pointwise field H = -grad u (the remark of Sec. 4.1-4.2 that computing H
+ * directly gives lower errors), from the whole-mesh charge route above:
+ *   4 pi H(r) = sum_{boundary faces F} int_F sigma(r') (r - r')/R^3 dA
+ *             + sum_t rho_t int_t (r - r')/R^3 dV.
+ * Volume term (divergence theorem, grad'(1/R) = (r - r')/R^3):
+ *   int_t (r - r')/R^3 dV = sum_{F of t} n_F int_F 1/R dA.
+ * Face term for an affine sigma(r') = sigma0 + g.(r' - rho0) on a plane
+ * triangle F (rho0 the projection of r, h = n.(r - rho0), Omega = int_F h/R^3
+ * the signed solid angle, and per edge e: outward in-plane normal m_e, unit
+ * tangent t_e, signed distance P0_e of rho0 to its line, Lambda_e =
+ * int_e 1/R dl, dR_e = R+ - R- the difference of the end distances):
+ * with r - r' = h n - (r' - rho0), the in-plane Gauss theorem
+ * int_F grad_s f dA = sum_e m_e int_e f dl applied to f = 1/R and to
+ * (r' - rho0)_a / R gives
+ *   int_F (r' - rho0)/R^3 dA = -sum_e m_e Lambda_e,
+ *   int_F (r' - rho0)(r' - rho0)^T/R^3 dA . g = Phi g - sum_e (m_e.g)(P0_e Lambda_e m_e + dR_e t_e),
+ * hence
+ *   int_F sigma (r - r')/R^3 dA = sigma0 Omega n - h (sum_e (g.m_e) Lambda_e) n + sigma0 sum_e Lambda_e m_e
+ *                                 - Phi g + sum_e (m_e.g)(P0_e Lambda_e m_e + dR_e t_e),
+ * Phi = int_F 1/R dA.  The point must not lie on a boundary face (the face
+ * term diverges there); on the line of an edge outside the edge Lambda_e is
+ * the finite log of the end distances.
+ * ------------------------------------------------------------------------- */
+static double edge_log(double lm, double lp, double R0, double Rm, double Rp, double tol) {
+  if (R0 > tol) return asinh(lp / R0) - asinh(lm / R0);
+  if (lm > tol) return log(lp / lm);     /* the point on the edge's line, before it */
+  if (lp < -tol) return log(lm / lp);    /* ... behind it */
+  (void)Rm; (void)Rp;
+  return NAN;                            /* on the edge itself */
+}
+
+static void face_field(const double r[3], const double* const V[3], const double n[3], double tol, double sigma0,
+                       const double g[3], double E[3], double* Phi_out) {
+  double ra[3];
+  sub3(r, V[0], ra);
+  const double h = dot3(n, ra), ah = fabs(h);
+  const double rho0[3] = {r[0] - h * n[0], r[1] - h * n[1], r[2] - h * n[2]};
+  double sum_log = 0, sum_beta = 0, gl = 0, A[3] = {0, 0, 0}, C[3] = {0, 0, 0};
+  for (int e = 0; e < 3; e++) {
+    const double* s = V[e];
+    const double* f = V[(e + 1) % 3];
+    double tv[3], t[3], m[3], ds[3], df[3], rs[3], rf[3];
+    sub3(f, s, tv);
+    const double L = norm3(tv);
+    t[0] = tv[0] / L; t[1] = tv[1] / L; t[2] = tv[2] / L;
+    cross3(t, n, m);
+    sub3(s, rho0, ds);
+    sub3(f, rho0, df);
+    const double lm = dot3(ds, t), lp = dot3(df, t);
+    const double P0 = dot3(ds, m);
+    sub3(s, r, rs);
+    sub3(f, r, rf);
+    const double Rm = norm3(rs), Rp = norm3(rf);
+    const double R02 = P0 * P0 + h * h, R0 = sqrt(R02);
+    const double Lam = edge_log(lm, lp, R0, Rm, Rp, tol);
+    if (fabs(P0) > tol) sum_log += P0 * Lam;
+    if (ah > tol && fabs(P0) > tol)
+      sum_beta += atan(P0 * lp / (R02 + ah * Rp)) - atan(P0 * lm / (R02 + ah * Rm));
+    const double gm = dot3(g, m);
+    gl += gm * Lam;
+    for (int a = 0; a < 3; a++) {
+      A[a] += Lam * m[a];
+      C[a] += gm * ((fabs(P0) > tol ? P0 * Lam : 0.0) * m[a] + (Rp - Rm) * t[a]);
+    }
+  }
+  const double Phi = sum_log - ah * sum_beta;
+  const double Omega = h > 0 ? sum_beta : (h < 0 ? -sum_beta : 0.0);
+  for (int a = 0; a < 3; a++) E[a] = sigma0 * Omega * n[a] - h * gl * n[a] + sigma0 * A[a] - Phi * g[a] + C[a];
+  if (Phi_out) *Phi_out = Phi;
+}
+
+/* H (B x n_pts x 3) at the points pts (n_pts x 3), none of them on a boundary
+ * face; boundary faces as (tet, local face) pairs. */
+int oracle_field_charges(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const int32_t* bfaces, int64_t n_bfaces, const double* M, int B, const double* pts,
+                         int64_t n_pts, double* H, int nthreads) {
+  if (!nodes || !tets || !M || !H || !pts || B < 1 || (n_bfaces && !bfaces)) return 1;
+#ifdef _OPENMP
+  /* thread count of this call only (a num_threads clause, not a global setting) */
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+  for (int64_t i = 0; i < n_pts; i++) {
+    const double* r = pts + 3 * i;
+    for (int b = 0; b < B; b++) {
+      double Hs[3] = {0, 0, 0};
+      for (int64_t t = 0; t < n_tets; t++) { /* volume charges: rho_t sum_F n_F Phi_F */
+        double v[12], Mt[12], Mr[3], J[9];
+        for (int k = 0; k < 4; k++) {
+          const int32_t gi = tets[4 * t + k];
+          for (int a = 0; a < 3; a++) {
+            v[3 * k + a] = nodes[3 * (int64_t)gi + a];
+            Mt[3 * k + a] = M[((int64_t)b * n_nodes + gi) * 3 + a];
+          }
+        }
+        tet_affine T;
+        tet_affine_init(v, &T);
+        tet_field(v, &T, Mt, r, Mr, J);
+        const double rho = -(J[0] + J[4] + J[8]);
+        if (rho == 0.0) continue;
+        for (int f = 0; f < 4; f++) {
+          int idx[3];
+          double n[3], I, K[3], h;
+          tet_face(v, f, idx, n);
+          const double* V[3] = {v + 3 * idx[0], v + 3 * idx[1], v + 3 * idx[2]};
+          face_charge_integrals(r, V, n, 1e-14 * T.diam, &I, K, &h);
+          for (int a = 0; a < 3; a++) Hs[a] += rho * n[a] * I;
+        }
+      }
+      for (int64_t q = 0; q < n_bfaces; q++) { /* boundary surface charges */
+        const int64_t t = bfaces[2 * q];
+        const int f = bfaces[2 * q + 1];
+        double v[12], Mt[12], Mr[3], J[9];
+        for (int k = 0; k < 4; k++) {
+          const int32_t gi = tets[4 * t + k];
+          for (int a = 0; a < 3; a++) {
+            v[3 * k + a] = nodes[3 * (int64_t)gi + a];
+            Mt[3 * k + a] = M[((int64_t)b * n_nodes + gi) * 3 + a];
+          }
+        }
+        tet_affine T;
+        tet_affine_init(v, &T);
+        tet_field(v, &T, Mt, r, Mr, J);
+        int idx[3];
+        double n[3], E[3];
+        tet_face(v, f, idx, n);
+        const double* V[3] = {v + 3 * idx[0], v + 3 * idx[1], v + 3 * idx[2]};
+        double ra[3];
+        sub3(r, V[0], ra);
+        const double h = dot3(n, ra);
+        const double Jn[3] = {J[0] * n[0] + J[1] * n[1] + J[2] * n[2], J[3] * n[0] + J[4] * n[1] + J[5] * n[2],
+                              J[6] * n[0] + J[7] * n[1] + J[8] * n[2]};
+        const double sigma0 = dot3(n, Mr) - h * dot3(n, Jn); /* n.M(rho0) */
+        const double JTn[3] = {J[0] * n[0] + J[3] * n[1] + J[6] * n[2], J[1] * n[0] + J[4] * n[1] + J[7] * n[2],
+                               J[2] * n[0] + J[5] * n[1] + J[8] * n[2]};
+        const double nn = dot3(JTn, n);
+        const double gs[3] = {JTn[0] - nn * n[0], JTn[1] - nn * n[1], JTn[2] - nn * n[2]};
+        face_field(r, V, n, 1e-14 * T.diam, sigma0, gs, E, NULL);
+        for (int a = 0; a < 3; a++) Hs[a] += E[a];
+      }
+      for (int a = 0; a < 3; a++) H[((int64_t)b * n_pts + i) * 3 + a] = Hs[a] / FOUR_PI;
+    }
+  }
+  return 0;
+}
+
 void oracle_tet_volumes(const double* nodes, const int32_t* tets, int64_t n_tets, double* vol) {
   for (int64_t t = 0; t < n_tets; t++) {
     double v[12];
