@@ -186,6 +186,25 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
  * Nodes that belong to no tet get their potential, and H = 0. */
 demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream);
 
+/* Pointwise field H = -grad u at the interior nodes (Sec. 4.1-4.2: computing H
+ * directly, instead of from the potential by mass lumping, gives lower
+ * errors): the gradient of the local expansions (L2P of -grad u) plus the field
+ * of the near tets' charges in closed form -- the affine surface charges n.M of
+ * their faces and the constant volume charges -div M.  At an interior node the
+ * face charges of the faces through the node cancel pairwise between the two
+ * tets of each face (M is continuous) and are left out.  At boundary nodes
+ * (nodes on a face of exactly one tet) the pointwise field is singular; there
+ * H holds the mass-lumped field of demag_eval.
+ *   M : batch x n_nodes x 3, u : batch x n_nodes, H : batch x n_nodes x 3; DEVICE
+ *       pointers; u as demag_eval returns it.
+ * FP64 plans (DEMAG_FP64) with tet sources; either near_mode.  The first call
+ * finds the boundary nodes (on the host) and allocates a device buffer of
+ * 3 x n_nodes x batch doubles kept by the plan.  Asynchronous on cuda_stream.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL or host pointers, batch out of range),
+ * DEMAG_ERR_UNSUPPORTED (other precisions or sources), DEMAG_ERR_OUT_OF_MEMORY,
+ * DEMAG_ERR_CUDA. */
+demag_status demag_eval_field(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream);
+
 /* Device-side status of the most recent evaluation of `plan` (demag_eval,
  * demag_eval_noalloc, or this plan's part of a demag_eval_multi submission).
  * Calls with device pointers are asynchronous, so a bounded device wait that

@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True):
         L.demag_plan_create.argtypes = [vp, i64, vp, i64, i32, i32, d, C.POINTER(demag_options), C.POINTER(vp)]
         L.demag_eval.restype = i32
         L.demag_eval.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.demag_eval_field.restype = i32
+        L.demag_eval_field.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_plan_debug.restype = i32
         L.demag_plan_debug.argtypes = [vp, i32]
         L.demag_eval_status.restype = i32
@@ -131,6 +133,11 @@ def demag_eval(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
 def demag_eval_status(plan, stream_ptr):
     """DEMAG_ERR_TIMEOUT if a bounded device wait expired in the plan's last evaluation (synchronises)."""
     return load().demag_eval_status(plan, stream_ptr)
+
+
+def demag_eval_field(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
+    """u and the pointwise field -grad u at the interior nodes (mass-lumped H at boundary nodes)."""
+    return load().demag_eval_field(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr)
 
 
 def demag_plan_debug(plan, flags):

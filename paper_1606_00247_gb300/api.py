@@ -92,6 +92,21 @@ class Plan:
             return u[0], (H[0] if with_H else None)
         return u, (H if with_H else None)
 
+    def eval_field(self, M, stream=None):
+        """u (B, N_n) and the pointwise field H = -grad u (B, N_n, 3) at the interior
+        nodes (mass-lumped H at the boundary nodes); FP64 plans with tet sources."""
+        M = _as_f64(M, self.device)
+        squeeze = M.dim() == 2
+        if squeeze:
+            M = M.unsqueeze(0)
+        B = int(M.shape[0])
+        u = torch.empty((B, self.n_nodes), dtype=torch.float64, device=self.device)
+        H = torch.empty((B, self.n_nodes, 3), dtype=torch.float64, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        L.check(L.demag_eval_field(self._h, M.data_ptr(), B, u.data_ptr(), H.data_ptr(), s.cuda_stream),
+                "demag_eval_field")
+        return (u[0], H[0]) if squeeze else (u, H)
+
     def energy(self, M, H, stream=None):
         """e[b] = -(1/2) sum_i V_i M_b,i . H_b,i (demag_energy; E = mu0 e), device tensors (B, N_n, 3)."""
         if M.dim() == 2:

@@ -375,6 +375,14 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
   });
 }
 
+demag_status demag_eval_field(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream) {
+  return guarded([&] {
+    if (!plan || !M || !u || !H) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
+    if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
+    eval_field(*plan, M, batch, u, H, (cudaStream_t)cuda_stream);
+  });
+}
+
 demag_status demag_plan_debug(demag_plan plan, int flags) {
   if (!plan || (flags & ~1)) {
     set_last_error("demag_plan_debug: NULL plan or unknown flag bits");

@@ -225,6 +225,9 @@ struct Plan {
   int64_t device_bytes = 0;
   Workspace* ws = nullptr;
   int* last_err = nullptr;          // device error flag of the most recent evaluation (demag_eval_status)
+  uint8_t* bnd_flag = nullptr;      // pointwise field: sorted nodes on a boundary face (on first use)
+  double* field_buf = nullptr;      // pointwise field: [sorted node][3][state]
+  int field_states = 0;
   int debug_flags = 0;              // demag_plan_debug: test hooks (bit 0: near-field stall)
 
   // per-stage timers (opt.profile) and launch counts
@@ -273,6 +276,8 @@ void dfree(Plan& P, void* ptr);  // one plan buffer, before the plan is destroye
 void build_plan(Plan& P, const double* nodes, const int32_t* tets);
 void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 void destroy_workspace(Plan& P);
+// pointwise field at the interior nodes (field.cu)
+void eval_field(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 
 // evaluation workspace (one per plan, sized for max_batch states)
 struct Workspace {
