@@ -193,12 +193,24 @@ def live_peaks():
     return peaks
 
 
-# FP64 operations of one (target node, source tet) pair in pair_contract
-# (p2p.cuh), counted from the source: 12 subtractions, 4 norms (5 each),
-# 6 edges x 4, 4 faces x (h 5, triple product 14, 3 dots 15, denominator 7,
-# 3 edges x 14, face combination 12), M(r) 18  -> 48+24+4*95+18 = 470, plus
-# 4 sqrt, 6 log1p, 6 divisions and 4 atan2.
-P2P_FLOPS_PER_PAIR = 470
+# FP64 operations of the on-the-fly near field per (target node, source tet)
+# pair, counted from the source (p2p.cuh, p2p.cu); sqrt, log1p, divisions and
+# atan2 are not counted.
+#  batches of fewer than P2P_AT_MIN_B states, pair_contract per pair and state:
+#   12 subtractions, 4 norms (5 each), 6 edges x 4, 4 faces x (h 5, triple
+#   product 14, 3 dots 15, denominator 7, 3 edges x 14, face combination 12),
+#   M(r) 18  -> 48+24+4*95+18 = 470 per state;
+#  larger batches, pair_at once per pair (12 + 20 + 24 + 1, then 4 faces x
+#   (h 5, triple product 14, 3 dots 15, denominator 8, Om and I 2, 3 edges x 69,
+#   a 12, T 87) = 1457) and 44 per state (M(r) 18, T:J 14, M(r).a + T:J/2 7,
+#   the warp's shuffle sum 5).
+P2P_AT_MIN_B = 2
+P2P_PAIR_FLOPS, P2P_STATE_FLOPS, P2P_PERSTATE_FLOPS = 1457, 44, 470
+
+
+def p2p_fp64_flops(B):
+    """FP64 flops of one (target node, source tet) pair for a batch of B states."""
+    return P2P_PERSTATE_FLOPS * B if B < P2P_AT_MIN_B else P2P_PAIR_FLOPS + P2P_STATE_FLOPS * B
 
 
 def m2l_macs(p):
@@ -312,12 +324,13 @@ def stage_roofline(stage, stats, steps_profiled, precision, peaks, sm_mhz, tenso
                     "note": f"algorithmic flops 2*C(p+6,6) per pair per state, {kind} CUDA cores"})
         return out
     if stage == "p2p" and stats["near_mode"] == 0:
-        work = stats["n_p2p_pairs"] * P2P_FLOPS_PER_PAIR * B / launches_per_eval
+        work = stats["n_p2p_pairs"] * p2p_fp64_flops(B) / launches_per_eval
         achieved = work / per_launch_s / 1e12
         peak, src = _alu_peak("fp64", peaks, sm_mhz)
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": NCU_TRAFFIC.get(key), "peak_source": src,
-                    "note": "FP64 pipe, 470 FP64 flops per (node, tet) pair and state; transcendentals not counted"})
+                    "note": (f"FP64 pipe, {p2p_fp64_flops(B)} FP64 flops per (node, tet) pair for {B} states "
+                             "(pair geometry once per pair from 2 states on); transcendentals not counted")})
         return out
     if stage == "p2p":
         # stored near field: every (target node, source node) coefficient triple read once per
@@ -438,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
     B = args.batch
     plan = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
                 near_mode=args.near_mode, max_batch=B, device=dev, autotune=int(args.autotune),
-                m2l_table_batch=args.m2l_table_batch, sources=args.sources)
+                m2l_table_batch=args.m2l_table_batch, m2l_split_degree=args.m2l_split_degree, sources=args.sources)
     st0 = plan.stats()
     w["leaf"] = st0["leaf_size"]  # the leaf kept by the leaf-size tuner (autotune bit 1), else the requested one
     w["p"] = st0["p"]  # the order kept by the order tuner (autotune bit 2), else the requested one
@@ -474,20 +487,24 @@ def run_ours(args, rank, world, local_rank):
     device_status = L.demag_status_string(L.demag_eval_status(plan.handle, stream.cuda_stream))
     total_ms, value = aggregate_ranks(total_ms, B * args.steps, world, dev)
 
-    # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside)
-    Mh = make_M(nodes.shape[0], B, seed_offset=rank, tets=tets, w=w)
-    plan.eval_host(Mh)
+    # end to end through the C ABI with host buffers (H2D of M, D2H of u and H inside the
+    # call), in pinned host memory
+    Mh = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64).pin_memory().numpy()
+    Mh[:] = make_M(nodes.shape[0], B, seed_offset=rank, tets=tets, w=w)
+    uh = torch.empty((B, nodes.shape[0]), dtype=torch.float64).pin_memory().numpy()
+    Hh = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64).pin_memory().numpy()
+    plan.eval_host(Mh, u=uh, H=Hh)
     t_e2e = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        plan.eval_host(Mh)
+        plan.eval_host(Mh, u=uh, H=Hh)
         t_e2e.append(time.perf_counter() - t0)
     e2e_value = world * B * args.steps / sum(t_e2e)
 
     # live per-stage timing pass (CUDA events on the eval stream, inside the library)
     prof = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
                 near_mode=args.near_mode, max_batch=B, device=dev, profile=True, autotune=int(args.autotune) & 1,
-                m2l_table_batch=args.m2l_table_batch, sources=args.sources)
+                m2l_table_batch=args.m2l_table_batch, m2l_split_degree=args.m2l_split_degree, sources=args.sources)
     for _ in range(2):
         prof.eval(M, u, H)
     prof.reset_timers()
@@ -554,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "n_tets": st0["n_tets"], "n_nodes": st0["n_nodes"],
                    "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_gpu": B,
                    "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
-                   "sources": args.sources,
+                   "sources": args.sources, "m2l_split_degree": ("p-4" if args.m2l_split_degree == 0 else "all"),
                    "parallelism": f"replicas x{world}", "n_cells": st0["n_cells"], "n_m2l": st0["n_m2l"],
                    "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
                    "plan_ms": st0["plan_ms"], "m2l_operators": st0["n_m2l_ops"],
@@ -565,7 +582,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "fp64_reference": ref_info,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Mh.nbytes),
-                "d2h_bytes_per_step": int(B * nodes.shape[0] * 4 * 8)},
+                "d2h_bytes_per_step": int(uh.nbytes + Hh.nbytes), "host_buffers": "pinned"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
@@ -591,7 +608,7 @@ def run_llg(args, rank, local_rank, w):
     B = args.batch
     pl = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision,
               near_mode=args.near_mode, max_batch=B, device=dev, autotune=int(args.autotune) & 1,
-              m2l_table_batch=args.m2l_table_batch)
+              m2l_table_batch=args.m2l_table_batch, m2l_split_degree=args.m2l_split_degree)
     m = torch.as_tensor(inputs.smoothed_unit_m(tets, nodes.shape[0], batch=B, seed=inputs.MAG_SEED + 9), device=dev)
     pl.llg_rk4(m, Ms=1.0, alpha=0.1, dt=0.02, steps=max(1, args.warmup))
     torch.cuda.synchronize(dev)
@@ -631,7 +648,7 @@ def run_multi(args, rank, world, local_rank, w):
     meshes = multi_meshes(w)
     B = args.batch
     kw = dict(p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision=args.precision, near_mode=args.near_mode,
-              max_batch=B, device=dev, autotune=int(args.autotune) & 1, m2l_table_batch=args.m2l_table_batch)
+              max_batch=B, device=dev, autotune=int(args.autotune) & 1, m2l_table_batch=args.m2l_table_batch, m2l_split_degree=args.m2l_split_degree)
     t0 = time.perf_counter()
     plans = [Plan(n, t, **kw) for n, t in meshes]
     plan_s = time.perf_counter() - t0
@@ -815,6 +832,9 @@ def main():
                          "bit 2: pick the smallest p meeting 5e-5 against FP64 p = 10 (-1: the workload's default)")
     ap.add_argument("--m2l-table-batch", type=int, default=0,
                     help="largest batch run by the FP32 table M2L in the tensor-core precisions (0: default, -1: never)")
+    ap.add_argument("--m2l-split-degree", type=int, default=0,
+                    help="split BF16 tensor-core M2L: 0 = second-limb products up to term degree p - 4 "
+                         "(default), < 0 = on every term")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--theta", type=float, default=0.0)

@@ -145,13 +145,22 @@ typedef struct {
                           arguments, including demag_plan_debug flags, are
                           those of the recorded call); 0 (default): every
                           call launches its kernels                         */
+  int m2l_split_degree; /* DEMAG_MIXED_BF16X3, tensor-core M2L: 0 (default)
+                          forms the products with the second BF16 limb
+                          (hi x lo, lo x hi) only for the terms of degree
+                          |m| + |n| <= p - 4 of the translation (Sec. 2.3);
+                          the four highest degrees, whose share of the
+                          expansion falls off like a power of the cell
+                          size over the distance, take hi x hi alone
+                          (about half the MMAs); < 0: both products for
+                          every term; > 0 is invalid                      */
 } demag_options;
 
 enum { DEMAG_SOURCES_TETS = 0, DEMAG_SOURCES_DIPOLES = 1, DEMAG_SOURCES_PATCHES = 2 };
 
 /* Defaults: p=4, leaf_size=32, theta=0.5, DEMAG_FP64, near_mode=0, max_batch=1,
  * autotune=0, profile=0, m2l_targets_per_cta=0, m2l_kps=0, m2l_promote=0, m2l_promote_rows=0,
- * m2l_table_batch=0, sources=0, near_tc=0, graph=0. */
+ * m2l_table_batch=0, sources=0, near_tc=0, graph=0, m2l_split_degree=0. */
 void demag_options_default(demag_options* opt);
 
 /* Build a plan (Sec. 3.1-3.3): octree over the bounding cube, radii, MAC and
@@ -319,7 +328,7 @@ enum {
   DEMAG_STAGE_M2L = 3,
   DEMAG_STAGE_L2L = 4,
   DEMAG_STAGE_L2P = 5,
-  DEMAG_STAGE_NEAR_PREP = 6, /* per-tet, per-state records of the near field */
+  DEMAG_STAGE_NEAR_PREP = 6, /* per-tet records of the FP64 on-the-fly near field, one state */
   DEMAG_STAGE_P2P = 7,
   DEMAG_STAGE_H = 8,         /* mass-lumped H and the output layout           */
   DEMAG_N_STAGES = 9

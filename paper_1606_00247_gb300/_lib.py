@@ -31,7 +31,7 @@ class demag_options(C.Structure):
                 ("m2l_targets_per_cta", C.c_int), ("m2l_kps", C.c_int),
                 ("m2l_promote", C.c_int), ("m2l_promote_rows", C.c_int),
                 ("m2l_table_batch", C.c_int), ("sources", C.c_int), ("near_tc", C.c_int),
-                ("graph", C.c_int)]
+                ("graph", C.c_int), ("m2l_split_degree", C.c_int)]
 
 
 DEMAG_N_STAGES = 9
@@ -68,9 +68,9 @@ def load(build_if_missing: bool = True):
         if _lib is not None:
             return _lib
         if not os.path.exists(LIB_PATH) and build_if_missing:
-            from . import build as _b
+            from .build import build  # the package exports the function under the module's name
 
-            _b.build()
+            build()
         if not os.path.exists(LIB_PATH):
             raise RuntimeError("libdemag.so is not built (run paper_1606_00247_gb300/build.py)")
         L = C.CDLL(LIB_PATH)

@@ -32,7 +32,8 @@ class Plan:
 
     def __init__(self, nodes, tets, p=4, leaf_size=32, theta=0.5, precision="fp64", near_mode=0, max_batch=1,
                  device="cuda", profile=False, autotune=False, m2l_targets_per_cta=0, m2l_kps=0,
-                 m2l_promote=0, m2l_promote_rows=0, m2l_table_batch=0, sources="tets", near_tc=0, graph=False):
+                 m2l_promote=0, m2l_promote_rows=0, m2l_table_batch=0, sources="tets", near_tc=0, graph=False,
+                 m2l_split_degree=0):
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
@@ -50,6 +51,7 @@ class Plan:
         opt.m2l_table_batch = int(m2l_table_batch)
         opt.sources = {"tets": 0, "dipoles": 1, "patches": 2}[sources] if isinstance(sources, str) else int(sources)
         opt.near_tc = int(near_tc)
+        opt.m2l_split_degree = int(m2l_split_degree)
         opt.graph = int(bool(graph))  # demag_eval with device pointers: record once, replay as a CUDA graph
         with torch.cuda.device(self.device):
             st, h = L.demag_plan_create(nodes_t.data_ptr(), self.n_nodes, tets_t.data_ptr(), self.n_tets, int(p),
@@ -135,15 +137,20 @@ class Plan:
                                 s.cuda_stream), "demag_llg_rk4")
         return m
 
-    def eval_host(self, M: np.ndarray, with_H=True):
-        """Same call with host (numpy) buffers: the library copies in and out."""
+    def eval_host(self, M: np.ndarray, with_H=True, u=None, H=None):
+        """Same call with host (numpy) buffers: the library copies in and out.
+        u and H may be given (e.g. views of pinned host memory, for fast copies)."""
         M = np.ascontiguousarray(M, dtype=np.float64)
         squeeze = M.ndim == 2
         if squeeze:
             M = M[None]
         B = M.shape[0]
-        u = np.empty((B, self.n_nodes))
-        H = np.empty((B, self.n_nodes, 3)) if with_H else None
+        if u is None:
+            u = np.empty((B, self.n_nodes))
+        if with_H and H is None:
+            H = np.empty((B, self.n_nodes, 3))
+        if not with_H:
+            H = None
         with torch.cuda.device(self.device):
             st = L.demag_eval(self._h, M.ctypes.data, B, u.ctypes.data, H.ctypes.data if with_H else None, None)
         L.check(st, "demag_eval")

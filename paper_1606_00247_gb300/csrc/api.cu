@@ -309,6 +309,7 @@ void demag_options_default(demag_options* o) {
   o->profile = 0;
   o->near_tc = 0;
   o->graph = 0;
+  o->m2l_split_degree = 0;
 }
 
 demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, int p,
@@ -335,6 +336,7 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
       fail(DEMAG_ERR_INVALID_ARG, "m2l_targets_per_cta must be 0, 1 or 2");
     if (o.m2l_kps < 0 || o.m2l_kps > 8) fail(DEMAG_ERR_INVALID_ARG, "m2l_kps must be in 0..8");
     if (o.m2l_promote_rows < 0 || o.m2l_promote_rows > 64) fail(DEMAG_ERR_INVALID_ARG, "m2l_promote_rows must be in 0..64");
+    if (o.m2l_split_degree > 0) fail(DEMAG_ERR_INVALID_ARG, "m2l_split_degree must be 0 (default) or < 0 (every term)");
     if (o.near_mode != 0 && o.near_mode != 1) fail(DEMAG_ERR_INVALID_ARG, "near_mode must be 0 or 1");
     if (o.sources != DEMAG_SOURCES_TETS && o.sources != DEMAG_SOURCES_DIPOLES && o.sources != DEMAG_SOURCES_PATCHES)
       fail(DEMAG_ERR_INVALID_ARG, "sources must be DEMAG_SOURCES_TETS, _DIPOLES or _PATCHES");

@@ -70,7 +70,8 @@ __host__ __device__ inline void mi_decode(int idx, int& a, int& b, int& c) {
 // faces have the fixed counter-clockwise vertex orders below.
 // ---------------------------------------------------------------------------
 constexpr int TET_GEO = 66;
-// per-tet, per-state record for the on-the-fly near field (56 doubles):
+// per-tet, per-state record for the on-the-fly near field of small batches
+// (56 doubles):
 //   [0..2] M(v0)  [3..11] J = dM/dx (row a = component)  [12..23] alpha_{F,e}
 //   [24..35] beta_{F,e}  [36..47] mu_{F,e}  [48..51] gamma_F  [52..55] eps_F
 constexpr int TET_STATE = 56;
@@ -182,6 +183,7 @@ struct Plan {
   int32_t* nf_cols = nullptr;       // sorted node of each column (groups padded with the last column)
   int32_t* nf_order = nullptr;      // ntiles: launch order, by decreasing column groups
   unsigned char* nf_W = nullptr;
+  float* nf_S = nullptr;            // nn x 3: row sums S_i = sum_j W_ij of the coefficients (FP64 sums)
 
   // tensor-core M2L (TF32 / split BF16): one operator tile set per distinct
   // (level difference, lattice offset) and the operator index of every pair
@@ -193,7 +195,7 @@ struct Plan {
   uint32_t* m2l_rc_items = nullptr; // row-chunk items (m | c << 16), then per row a CSR of its items
   int m2l_rc_nitems = 0, m2l_rc_ch = 0;
   int tc_nt = 1, tc_kps = 0, tc_budget = 0;  // M2L launch shape: targets per CTA, k-steps per slot, ring bytes
-  int tc_l3 = 0;                    // split BF16: k-steps in three limbs (0 = none, 99 = all)
+  int tc_ls = 0;                    // split BF16 limb scheme of the tensor-core M2L (m2l_tc.cu)
   int tc_prom_group = 0, tc_prom_rows = 16;  // accumulator promotion: sources per group (0 = off), rows
   int64_t* tc_g1_off = nullptr;     // one-target groups: list offsets in target order
   int64_t tc_n_g2 = 0;              // two-target groups (consecutive targets), union lists:
@@ -353,8 +355,14 @@ bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, 
 
 // near field (p2p.cu)
 void build_tet_geometry(Plan& P);
+// FP64 on-the-fly near field.  Batches of P2P_AT_MIN_B states or more: the
+// pair geometry once per (target, tet), contracted with every state (Ms);
+// smaller batches: pair by pair and state by state on the per-tet records
+// of launch_tet_state (state).
+constexpr int P2P_AT_MIN_B = 2;
 void launch_tet_state(Plan& P, const double* Ms, int B, double* state, cudaStream_t s);
-void launch_p2p_fp64(Plan& P, const double* state, int B, double* u_s, int* err_flag, cudaStream_t s);
+void launch_p2p_fp64(Plan& P, const double* Ms, const double* state, int B, double* u_s, int* err_flag,
+                     cudaStream_t s);
 
 }  // namespace demag
 

@@ -332,7 +332,7 @@ Workspace& workspace(Plan& P, int B) {
     if (mp) W->MP = (float*)ws_alloc(*W, sizeof(float) * mp);
   }
   if (!mixed || otf) W->u_s = (double*)ws_alloc(*W, sizeof(double) * nn * need);  // FP64 sorted u
-  if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * need);
+  if (otf) W->state = (double*)ws_alloc(*W, sizeof(double) * nt * TET_STATE * std::min(need, P2P_AT_MIN_B - 1));
   W->err = (int*)ws_alloc(*W, sizeof(int));  // staging for host M, u, H: at the first host-pointer call
   P.ws = W;
   return *W;
@@ -426,13 +426,15 @@ void near_field_fp64(Plan& P, Workspace& W, int B, StageClock& clk, cudaStream_t
     clk.end();
     return;
   }
-  clk.begin(DEMAG_STAGE_NEAR_PREP);
-  launch_tet_state(P, W.Ms, B, W.state, s);
-  clk.launched();
-  clk.end();
+  if (B < P2P_AT_MIN_B) {
+    clk.begin(DEMAG_STAGE_NEAR_PREP);
+    launch_tet_state(P, W.Ms, B, W.state, s);
+    clk.launched();
+    clk.end();
+  }
   clk.begin(DEMAG_STAGE_P2P);
   if (!P.h_p2p_targets.empty()) {
-    launch_p2p_fp64(P, W.state, B, W.u_s, W.err, s);
+    launch_p2p_fp64(P, W.Ms, W.state, B, W.u_s, W.err, s);
     clk.launched();
   }
   clk.end();

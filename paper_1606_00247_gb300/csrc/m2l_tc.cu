@@ -90,24 +90,50 @@ struct Tmp {
 // kernels; also evaluated on the host for the operator table and the packing)
 struct TcLayout {
   int valid, bf16;
-  int l3;                           // split BF16: leading k-steps carried in three limbs (the rest in two)
+  int ls;                           // split BF16 limb scheme: TC_LS_ALL2, TC_LS_ALL3 or a split degree (below)
   int lmax;                         // most limbs of any k-step (A slices are lmax x 4 KB apart)
   int E, KW;                        // elements per 16 bytes, per k-step (2E)
   int nc, ncp;                      // coefficients, padded to 16 (TMEM columns used)
   int KS;                           // k-steps of the A tile
   int Nks[TC_MAXKS];                // rows used at k-step ks (a prefix), padded to 16
+  int N2[TC_MAXKS];                 // rows that also take the products with a second limb (a prefix of Nks)
+  int L[TC_MAXKS];                  // limbs of k-step ks (A slices and operator rows)
   int ks_off[TC_MAXKS + 1];         // byte offset of k-step ks within one operator
   int op_bytes;                     // one operator, all k-steps, all limbs
-  int a_bytes;                      // stride of the A slices of consecutive k-steps (lmax limbs)
+  int a_off[TC_MAXKS + 1];          // byte offset of k-step ks within the A tile of one (cell, 128 states):
+                                    // its L[ks] limb slices, 4 KB each, k-steps contiguous
+  int a_bytes;                      // the whole A tile
   int tmem_cols;                    // power of two >= ncp
 };
 
 __host__ __device__ constexpr int cnc_of(int t) { return t < 0 ? 0 : (t + 1) * (t + 2) * (t + 3) / 6; }
 __host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
-// operand limbs of k-step ks: TF32 1; split BF16 3 for the leading l3 k-steps, else 2
-__host__ __device__ constexpr int limbs_of(bool bf16, int l3, int ks) { return bf16 ? (ks < l3 ? 3 : 2) : 1; }
+__host__ __device__ constexpr int tri3(int t) { return t * (t + 1) * (t + 2) / 6; }
+// degree of the multi-index at position m of the graded order
+__host__ __device__ constexpr int degree_of(int m) {
+  int t = 0;
+  while (tri3(t + 1) <= m) t++;
+  return t;
+}
 
-__host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int l3) {
+// Split BF16 limb schemes.  Every product of the operator K (rows m) and the
+// moments A (columns n) has a term degree |m| + |n| <= p.
+//   TC_LS_ALL2: two limbs (16 significant bits) everywhere, three MMAs per
+//               k-step (hi x hi, hi x lo, lo x hi) over all its rows;
+//   TC_LS_ALL3: three limbs (24 bits), six MMAs per k-step;
+//   d in 1..2p: the products hi x lo and lo x hi only where |m| + |n| <= d
+//               (for the k-step's lowest |n|); the other terms take hi x hi
+//               alone (8 significant bits per operand).  Terms of high degree
+//               carry the smallest share of the expansion (they fall off like
+//               the ratio of cell size to distance to that power), so their
+//               8-bit products stay below the error of the low-degree terms;
+//               k-steps with no such rows keep one limb and one MMA.
+constexpr int TC_LS_ALL2 = 0, TC_LS_ALL3 = 99;
+// default split degree: p - TC_SD_BELOW (the four highest term degrees of the
+// expansion take hi x hi alone)
+constexpr int TC_SD_BELOW = 4;
+
+__host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int ls) {
   TcLayout G{};
   if (p < 1 || p > 12) return G;
   G.bf16 = bf16 ? 1 : 0;
@@ -117,18 +143,37 @@ __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int l3) {
   G.ncp = pad_to(G.nc, 16);
   G.KS = pad_to(G.nc, G.KW) / G.KW;
   if (G.KS > TC_MAXKS) return TcLayout{};
-  G.l3 = bf16 ? (l3 < 0 ? 0 : (l3 > G.KS ? G.KS : l3)) : 0;
-  G.lmax = bf16 ? (G.l3 > 0 ? 3 : 2) : 1;
+  G.ls = bf16 ? ls : TC_LS_ALL2;
+  G.lmax = 1;
   G.ks_off[0] = 0;
   for (int ks = 0; ks < G.KS; ks++) {
     int rows = 0;  // rows of degree t need n < cnc(p - t)
     for (int t = 0; t <= p; t++)
       if (cnc_of(p - t) > ks * G.KW) rows = cnc_of(t);
     G.Nks[ks] = pad_to(rows, 16);
-    G.ks_off[ks + 1] = G.ks_off[ks] + limbs_of(bf16, G.l3, ks) * 32 * G.Nks[ks];
+    if (!bf16) {
+      G.L[ks] = 1;
+      G.N2[ks] = 0;
+    } else if (ls == TC_LS_ALL3) {
+      G.L[ks] = 3;
+      G.N2[ks] = G.Nks[ks];
+    } else if (ls == TC_LS_ALL2) {
+      G.L[ks] = 2;
+      G.N2[ks] = G.Nks[ks];
+    } else {
+      const int r = ls - degree_of(ks * G.KW);  // rows of degree <= r take the second limb
+      const int n2 = r < 0 ? 0 : pad_to(cnc_of(r), 16);
+      G.N2[ks] = n2 < G.Nks[ks] ? n2 : G.Nks[ks];
+      G.L[ks] = G.N2[ks] > 0 ? 2 : 1;
+    }
+    if (G.L[ks] > G.lmax) G.lmax = G.L[ks];
+    // the chunk of a k-step: hi rows (Nks), then each further limb's rows (N2)
+    G.ks_off[ks + 1] = G.ks_off[ks] + 32 * (G.Nks[ks] + (G.L[ks] - 1) * G.N2[ks]);
   }
   G.op_bytes = G.ks_off[G.KS];
-  G.a_bytes = G.lmax * TC_SLICE;
+  G.a_off[0] = 0;
+  for (int ks = 0; ks < G.KS; ks++) G.a_off[ks + 1] = G.a_off[ks] + G.L[ks] * TC_SLICE;
+  G.a_bytes = G.a_off[G.KS];
   int tc = 32;
   while (tc < G.ncp) tc *= 2;
   if (tc > 512) return TcLayout{};
@@ -138,34 +183,40 @@ __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int l3) {
 }
 
 // the orders with a compiled tensor-core kernel; split BF16 is compiled with
-// two limbs on every k-step (DEMAG_MIXED_BF16X3) or three (DEMAG_MIXED_BF16X6)
+// the default split degree of the order and with two limbs on every k-step
+// (DEMAG_MIXED_BF16X3), and with three limbs (DEMAG_MIXED_BF16X6)
 constexpr bool tc_order(int p) { return p == 4 || p == 6 || p == 8 || p == 10; }
-constexpr int TC_L3_ALL = 99;
+__host__ __device__ constexpr int tc_split_degree(int p) { return p - TC_SD_BELOW; }
 
 // launch shape: `nt` targets per CTA sharing each source's moments, `kps`
 // k-steps of one source per ring slot (A slices, then one K region per target)
 struct TcRing {
-  int nt, kps, nsteps, kmax, slot_bytes, nslots;
+  int nt, kps, nsteps, amax, kmax, slot_bytes, nslots;
   int prom_group, prom_chunks;                  // promote the first prom_chunks x 16 columns every prom_group sources
   int step_koff[TC_MAXKS], step_kb[TC_MAXKS];  // K bytes of step st within one operator
+  int step_aoff[TC_MAXKS], step_ab[TC_MAXKS];  // A bytes of step st within one A tile
 };
 
 bool make_ring(const TcLayout& G, int nt, int kps, int budget, TcRing& R) {
   if (!G.valid || kps < 1 || kps > G.KS || nt < 1 || nt > 2) return false;
-  if (nt == 2 && (G.tmem_cols > 256 || G.l3 > 0)) return false;  // two accumulators in 512 columns; compiled for two limbs
+  if (nt == 2 && (G.tmem_cols > 256 || G.ls == TC_LS_ALL3)) return false;  // two accumulators in 512 columns
   R = TcRing{};
   R.nt = nt;
   R.kps = kps;
   R.nsteps = (G.KS + kps - 1) / kps;
-  int maxk = 0;
+  int maxk = 0, maxa = 0;
   for (int st = 0; st < R.nsteps; st++) {
     const int k0 = st * kps, k1 = std::min(k0 + kps, G.KS);
     R.step_koff[st] = G.ks_off[k0];
     R.step_kb[st] = G.ks_off[k1] - G.ks_off[k0];
+    R.step_aoff[st] = G.a_off[k0];
+    R.step_ab[st] = G.a_off[k1] - G.a_off[k0];
     maxk = std::max(maxk, R.step_kb[st]);
+    maxa = std::max(maxa, R.step_ab[st]);
   }
   R.kmax = maxk;
-  R.slot_bytes = pad_to(kps * G.a_bytes + nt * maxk, 1024);
+  R.amax = maxa;
+  R.slot_bytes = pad_to(maxa + nt * maxk, 1024);
   R.nslots = std::min(32, budget / R.slot_bytes);
   return R.nslots >= 2;
 }
@@ -175,7 +226,6 @@ size_t ring_smem(const TcRing& R) { return (size_t)R.nslots * R.slot_bytes + siz
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__host__ __device__ constexpr int tri3(int t) { return t * (t + 1) * (t + 2) / 6; }
 __host__ __device__ constexpr int idx3(int a, int b, int c) {
   return tri3(a + b + c) + (b + c) * (b + c + 1) / 2 + c;
 }
@@ -319,16 +369,17 @@ __device__ __forceinline__ void store_row64(unsigned char* dst, int stride, int 
 }
 
 // ---------------------------------------------------------------------------
-// moments -> tile layout: QP[cell][sb][ks][limb][128 rows x 32 bytes] (k-steps a_bytes apart)
+// moments -> tile layout: QP[cell][sb] = A tile (k-step ks at a_off[ks]: [limb][128 rows x 32 bytes])
 template <bool BF16>
-__global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ Q, int nc, int B, int nsb, int KS,
-                                                      int a_bytes, int l3, unsigned char* __restrict__ QP) {
+__global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ Q, int nc, int B, int nsb,
+                                                      const TcLayout G, unsigned char* __restrict__ QP) {
+  const int KS = G.KS;
   constexpr int E = BF16 ? 8 : 4;
   const int64_t cell = blockIdx.x;
   const int sb = blockIdx.y, b = threadIdx.x, bb = sb * TC_M + b;
   const bool alive = bb < B;
   const float* q = Q + cell * nc * (int64_t)B + bb;
-  unsigned char* out = QP + (cell * nsb + sb) * (int64_t)KS * a_bytes;
+  unsigned char* out = QP + (cell * nsb + sb) * (int64_t)G.a_bytes;
   for (int qq = 0; qq < 2 * KS; qq++) {
     float v[E];
 #pragma unroll
@@ -336,8 +387,8 @@ __global__ void __launch_bounds__(TC_M) k_m2l_tc_pack(const float* __restrict__ 
       const int n = qq * E + u;
       v[u] = (alive && n < nc) ? q[(int64_t)n * B] : 0.f;
     }
-    const int off = (qq >> 1) * a_bytes + (b >> 3) * 256 + (qq & 1) * 128 + (b & 7) * 16;
-    store_row<BF16>(out + off, TC_SLICE, limbs_of(BF16, l3, qq >> 1), v);
+    const int off = G.a_off[qq >> 1] + (b >> 3) * 256 + (qq & 1) * 128 + (b & 7) * 16;
+    store_row<BF16>(out + off, TC_SLICE, G.L[qq >> 1], v);
   }
 }
 
@@ -390,16 +441,9 @@ __global__ void __launch_bounds__(128) k_m2l_tc_ops(const int4* __restrict__ key
         }
       }
       const int off = (r >> 3) * 256 + kc * 128 + (r & 7) * 16;
-      store_row64<BF16>(chunk + off, 32 * N, limbs_of(BF16, G.l3, ks), v);
+      store_row64<BF16>(chunk + off, 32 * N, r < G.N2[ks] ? G.L[ks] : 1, v);
     }
   }
-}
-
-// degree of the multi-index at position m of the graded order
-__host__ __device__ constexpr int degree_of(int m) {
-  int t = 0;
-  while (tri3(t + 1) <= m) t++;
-  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -409,14 +453,13 @@ __host__ __device__ constexpr int degree_of(int m) {
 // when e is not in its list.  Warp 0 lane 0 streams each source's A slices
 // once, plus the K slices of every target that uses it; warp 1 (target 0) and
 // warp 3 (target 1) issue the MMAs into their own 256-column halves of TMEM.
-template <int P, bool BF16, int NT, int L3>
+template <int P, bool BF16, int NT, int LS>
 __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
     k_m2l_tc(const int32_t* __restrict__ gtarget, const int64_t* __restrict__ goff,
              const int32_t* __restrict__ gsrc, const int32_t* __restrict__ gop, const int32_t* __restrict__ level,
              double side, int nc, int B, int nsb, const TcRing R, const unsigned char* __restrict__ QP,
              const unsigned char* __restrict__ ops, float* L, int* err) {
-  constexpr TcLayout G = tc_layout(P, BF16, L3);
-  constexpr bool A_UNIFORM = !BF16 || G.l3 == 0 || G.l3 >= G.KS;  // every k-step has lmax limbs
+  constexpr TcLayout G = tc_layout(P, BF16, LS);
   static_assert(G.valid, "no tensor-core layout for this order");
   static_assert(NT == 1 || G.tmem_cols <= 256, "two targets need two 256-column accumulators");
   constexpr int TMEM_COLS = NT == 1 ? G.tmem_cols : 512;
@@ -430,8 +473,10 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* counts = (int*)(tmem_slot + 2);  // slots issued, slots consumed by each issuer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t grp = blockIdx.x;
-  const int sb = blockIdx.y;
+  // the state blocks of a group are neighbours in launch order, so the second
+  // finds the group's translation operators in L2
+  const int64_t grp = blockIdx.x / nsb;
+  const int sb = (int)(blockIdx.x - grp * nsb);
   const int64_t e0 = goff[grp], e1 = goff[grp + 1];
   if (tid == 0) {
     for (int i = 0; i < R.nslots; i++) {
@@ -474,34 +519,24 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
 #pragma unroll
           for (int t = 0; t < NT; t++) On[t] = gop[(e + 1) * NT + t];
         }
-        const unsigned char* a = QP + ((int64_t)S * nsb + sb) * (int64_t)(G.KS * G.a_bytes);
+        const unsigned char* a = QP + ((int64_t)S * nsb + sb) * (int64_t)G.a_bytes;
         for (int st = 0; st < R.nsteps; st++) {
           if (n >= R.nslots && !mbar_wait(empty0 + 8 * slot, phase ^ 1u, abort_flag)) {
             if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
             *abort_flag = 1;
             break;
           }
-          const int k0 = st * R.kps, nk = min(R.kps, G.KS - k0);
           const uint32_t fb = full0 + 8 * slot, dst = ring0 + slot * R.slot_bytes;
-          const uint32_t kb = (uint32_t)R.step_kb[st];
-          uint32_t ab = 0;  // A bytes of the step: the used limbs of each k-step
-          for (int j = 0; j < nk; j++) ab += (uint32_t)(limbs_of(BF16, G.l3, k0 + j) * TC_SLICE);
-          uint32_t bytes = ab;
+          const uint32_t kb = (uint32_t)R.step_kb[st], ab = (uint32_t)R.step_ab[st];
+          uint32_t bytes = ab;  // the step's A slices (contiguous), then the K slices of each target
 #pragma unroll
           for (int t = 0; t < NT; t++) bytes += O[t] >= 0 ? kb : 0u;
           expect_tx(fb, bytes);
-          if (A_UNIFORM) {
-            bulk_load(dst, a + (int64_t)k0 * G.a_bytes, ab, fb);
-          } else {
-            for (int j = 0; j < nk; j++)
-              bulk_load(dst + j * G.a_bytes, a + (int64_t)(k0 + j) * G.a_bytes,
-                        (uint32_t)(limbs_of(BF16, G.l3, k0 + j) * TC_SLICE), fb);
-          }
+          bulk_load(dst, a + R.step_aoff[st], ab, fb);
 #pragma unroll
           for (int t = 0; t < NT; t++)
             if (O[t] >= 0)
-              bulk_load(dst + R.kps * G.a_bytes + t * R.kmax, ops + (int64_t)O[t] * G.op_bytes + R.step_koff[st], kb,
-                        fb);
+              bulk_load(dst + R.amax + t * R.kmax, ops + (int64_t)O[t] * G.op_bytes + R.step_koff[st], kb, fb);
           n++;
           if (++slot == R.nslots) {
             slot = 0;
@@ -528,7 +563,7 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
       for (int64_t e = e0; e < e1 && !bad; e++) {
         const int32_t On = NT == 1 ? 0 : (e + 1 < e1 ? gop[(e + 1) * NT + t] : -1);
         int j = 0;
-        uint32_t sa = 0, kb0 = 0;
+        uint32_t sa = 0, kb0 = 0, a0 = 0;
 #pragma unroll
         for (int ks = 0; ks < G.KS; ks++) {
           if (!bad && j == 0) {
@@ -539,28 +574,31 @@ __global__ void __launch_bounds__(TC_THREADS, NT == 1 ? 2 : 1)
             }
             tc_fence_after();
             sa = ring0 + slot * R.slot_bytes;
-            kb0 = sa + R.kps * G.a_bytes + t * R.kmax - G.ks_off[ks];
+            kb0 = sa + R.amax + t * R.kmax - G.ks_off[ks];
+            a0 = sa - G.a_off[ks];
           }
           if (!bad) {
             if (O >= 0) {
-              const uint32_t as = sa + j * G.a_bytes;
+              const uint32_t as = a0 + G.a_off[ks];
               const uint64_t ad = sdesc(as);
               const uint32_t kc = kb0 + G.ks_off[ks];  // k-step chunk: hi rows, then lo rows
-              const int nl = limbs_of(BF16, G.l3, ks);  // 1, 2 or 3 (compile-time after unrolling)
+              const int nl = G.L[ks];  // 1, 2 or 3 (compile-time after unrolling)
 #pragma unroll
               for (int r0 = 0; r0 < 512; r0 += 256) {
                 if (r0 < G.Nks[ks]) {
                   const int nrow = (G.Nks[ks] - r0 < 256) ? G.Nks[ks] - r0 : 256;  // MMA N <= 256
                   const uint32_t id = idesc(BF16 ? 1 : 2, TC_M, nrow);
                   const uint32_t dcol = tmem + t * 256 + r0;
-                  const uint32_t kl = 32 * G.Nks[ks];  // K limbs are 32 N bytes apart
+                  const uint32_t kl = 32 * G.Nks[ks];  // the second limb's rows follow the hi rows
                   const uint64_t bd = sdesc(kc + 32 * r0);
                   mma<BF16>(dcol, ad, bd, id, ks == 0 ? acc : 1u);
-                  if (nl >= 2) {  // products of limb orders 1: hi x mid, mid x hi
-                    mma<BF16>(dcol, ad, sdesc(kc + kl + 32 * r0), id, 1u);
-                    mma<BF16>(dcol, sdesc(as + TC_SLICE), bd, id, 1u);
+                  if (nl >= 2 && r0 < G.N2[ks]) {  // products of limb orders 1 on the rows that take them
+                    const int nrow2 = (G.N2[ks] - r0 < 256) ? G.N2[ks] - r0 : 256;
+                    const uint32_t id2 = idesc(1, TC_M, nrow2);
+                    mma<BF16>(dcol, ad, sdesc(kc + kl + 32 * r0), id2, 1u);
+                    mma<BF16>(dcol, sdesc(as + TC_SLICE), bd, id2, 1u);
                   }
-                  if (nl >= 3) {  // limb order 2: hi x lo, mid x mid, lo x hi
+                  if (nl >= 3) {  // limb order 2 (three limbs: N2 = Nks): hi x lo, mid x mid, lo x hi
                     mma<BF16>(dcol, ad, sdesc(kc + 2 * kl + 32 * r0), id, 1u);
                     mma<BF16>(dcol, sdesc(as + TC_SLICE), sdesc(kc + kl + 32 * r0), id, 1u);
                     mma<BF16>(dcol, sdesc(as + 2 * TC_SLICE), bd, id, 1u);
@@ -693,42 +731,49 @@ struct KeyHash {
 bool split_bf16(const Plan& P) {
   return P.opt.precision == DEMAG_MIXED_BF16X3 || P.opt.precision == DEMAG_MIXED_BF16X6;
 }
-TcLayout layout_of(const Plan& P) { return tc_layout(P.p, split_bf16(P), P.tc_l3); }
+TcLayout layout_of(const Plan& P) { return tc_layout(P.p, split_bf16(P), P.tc_ls); }
 
-template <int PP, bool BF16, int NT, int L3>
+template <int PP, bool BF16, int NT, int LS>
 void launch_fixed(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
   static size_t attr = 0;
   const size_t smem = ring_smem(R);
   if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT, L3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
   const int nsb = (B + TC_M - 1) / TC_M;
   if (NT == 1) {
-    dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)nsb);
-    k_m2l_tc<PP, BF16, NT, L3><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.tc_g1_off, P.m2l_src, P.m2l_op,
+    dim3 grid((unsigned)(nsb * P.h_m2l_targets.size()));
+    k_m2l_tc<PP, BF16, NT, LS><<<grid, TC_THREADS, smem, s>>>(P.m2l_targets, P.tc_g1_off, P.m2l_src, P.m2l_op,
                                                               P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L,
                                                               err);
   } else {
-    dim3 grid((unsigned)P.tc_n_g2, (unsigned)nsb);
-    k_m2l_tc<PP, BF16, NT, L3><<<grid, TC_THREADS, smem, s>>>(P.tc_g2_tgt, P.tc_g2_off, P.tc_g2_src, P.tc_g2_op,
+    dim3 grid((unsigned)(nsb * P.tc_n_g2));
+    k_m2l_tc<PP, BF16, NT, LS><<<grid, TC_THREADS, smem, s>>>(P.tc_g2_tgt, P.tc_g2_off, P.tc_g2_src, P.tc_g2_op,
                                                               P.cell_level, P.side, P.nc, B, nsb, R, QP, P.tc_ops, L,
                                                               err);
   }
   DM_LAUNCH("k_m2l_tc");
 }
 
-// compiled variants: TF32 and two-limb split BF16 with one or two targets per
-// CTA; three-limb split BF16 with one target per CTA
+// compiled variants: TF32, and split BF16 with the order's default split
+// degree or two limbs everywhere, with one or two targets per CTA; three-limb
+// split BF16 with one target per CTA
+template <int PP, bool BF16, int LS>
+void launch_ls(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
+  if constexpr (tc_layout(PP, BF16, LS).tmem_cols <= 256) {
+    if (R.nt == 2) return launch_fixed<PP, BF16, 2, LS>(P, R, B, QP, L, err, s);
+  }
+  launch_fixed<PP, BF16, 1, LS>(P, R, B, QP, L, err, s);
+}
+
 template <int PP, bool BF16>
 void launch_nt(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
   if constexpr (BF16) {
-    if (P.tc_l3 == TC_L3_ALL) return launch_fixed<PP, BF16, 1, TC_L3_ALL>(P, R, B, QP, L, err, s);
+    if (P.tc_ls == TC_LS_ALL3) return launch_fixed<PP, BF16, 1, TC_LS_ALL3>(P, R, B, QP, L, err, s);
+    if (P.tc_ls == tc_split_degree(PP)) return launch_ls<PP, BF16, tc_split_degree(PP)>(P, R, B, QP, L, err, s);
   }
-  if constexpr (tc_layout(PP, BF16, 0).tmem_cols <= 256) {
-    if (R.nt == 2) return launch_fixed<PP, BF16, 2, 0>(P, R, B, QP, L, err, s);
-  }
-  launch_fixed<PP, BF16, 1, 0>(P, R, B, QP, L, err, s);
+  launch_ls<PP, BF16, TC_LS_ALL2>(P, R, B, QP, L, err, s);
 }
 
 template <bool BF16>
@@ -770,10 +815,10 @@ void default_ring(const TcLayout& G, int nt, int kps, TcRing& R) {
 void tune_ring(Plan& P, const TcLayout& G) {
   cudaStream_t s = P.stream;
   const int B = TC_M;
-  Tmp<unsigned char> qp((size_t)P.ncells * G.KS * G.a_bytes);
+  Tmp<unsigned char> qp((size_t)P.ncells * G.a_bytes);
   Tmp<float> L((size_t)P.ncells * P.nc * B);
   Tmp<int> err(1);
-  DM_CUDA(cudaMemsetAsync(qp.p, 0, (size_t)P.ncells * G.KS * G.a_bytes, s));
+  DM_CUDA(cudaMemsetAsync(qp.p, 0, (size_t)P.ncells * G.a_bytes, s));
   DM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
   cudaEvent_t a, b;
   DM_CUDA(cudaEventCreate(&a));
@@ -879,7 +924,9 @@ void build_m2l_tc(Plan& P, const M2lKeys& K) {
   if (!K.ok || !tc_order(P.p)) return;  // the CUDA-core M2L runs instead
   P.tc_prom_group = P.opt.m2l_promote < 0 ? 0 : (P.opt.m2l_promote == 0 ? 8 : P.opt.m2l_promote);
   P.tc_prom_rows = P.opt.m2l_promote_rows > 0 ? P.opt.m2l_promote_rows : 16;
-  P.tc_l3 = P.opt.precision == DEMAG_MIXED_BF16X6 ? TC_L3_ALL : 0;
+  P.tc_ls = P.opt.precision == DEMAG_MIXED_BF16X6
+                ? TC_LS_ALL3
+                : (P.opt.m2l_split_degree < 0 ? TC_LS_ALL2 : tc_split_degree(P.p));
   const TcLayout G = layout_of(P);
   if (!G.valid) return;
   cudaStream_t s = P.stream;
@@ -945,7 +992,7 @@ size_t m2l_tc_pack_bytes(const Plan& P, int B) {
   if (B <= m2l_table_batch(P) && P.m2l_tab != nullptr) return 0;  // the table-driven M2L runs instead
   const TcLayout G = layout_of(P);
   const size_t nsb = (size_t)(B + TC_M - 1) / TC_M;
-  return (size_t)P.ncells * nsb * G.KS * G.a_bytes;
+  return (size_t)P.ncells * nsb * G.a_bytes;
 }
 
 bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, int* err, cudaStream_t s) {
@@ -957,9 +1004,9 @@ bool launch_m2l_tc(Plan& P, int B, const float* Q, unsigned char* QP, float* L, 
   const int nsb = (B + TC_M - 1) / TC_M;
   const dim3 grid((unsigned)P.ncells, (unsigned)nsb);
   if (G.bf16)
-    k_m2l_tc_pack<true><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, G.l3, QP);
+    k_m2l_tc_pack<true><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G, QP);
   else
-    k_m2l_tc_pack<false><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G.KS, G.a_bytes, G.l3, QP);
+    k_m2l_tc_pack<false><<<grid, TC_M, 0, s>>>(Q, P.nc, B, nsb, G, QP);
   DM_LAUNCH("k_m2l_tc_pack");
   launch_main(P, R, B, QP, L, err, s);
   return true;

@@ -649,6 +649,25 @@ __global__ void k_nf_pack(const int32_t* __restrict__ targets, const int4* __res
   }
 }
 
+// row sums of the near-field coefficients, S_i = sum_j W_ij (FP64, columns in
+// order), per sorted target node: the tensor-core near field applies W to
+// M - Mbar and adds S_i . Mbar (near_tc.cu)
+__global__ void k_nf_rowsum(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+                            const int64_t* __restrict__ lcoloff, const int64_t* __restrict__ lwoff,
+                            const double* __restrict__ W, float* S) {
+  const int64_t l = blockIdx.x;
+  const int4 rT = range[targets[l]];
+  const int nT = rT.w - rT.z;
+  const int64_t ncol = lcoloff[l + 1] - lcoloff[l];
+  const double* Wl = W + lwoff[l];
+  for (int q = threadIdx.x; q < 3 * nT; q += blockDim.x) {
+    const int i = q / 3, comp = q - 3 * i;
+    double acc = 0.0;
+    for (int64_t c = 0; c < ncol; c++) acc += Wl[(c * nT + i) * 3 + comp];
+    S[(int64_t)(rT.z + i) * 3 + comp] = (float)acc;
+  }
+}
+
 }  // namespace
 
 // Tiles of the tensor-core near field over the P2P target leaves (already in
@@ -894,6 +913,8 @@ void build_near_field(Plan& P) {
     P.nf_rownode = dalloc<int32_t>(P, rown.size());
     P.nf_cols = dalloc<int32_t>(P, std::max<int64_t>(P.nf_ncols, 1));
     P.nf_W = dalloc<unsigned char>(P, std::max<int64_t>(P.nf_wbytes, 16));
+    P.nf_S = dalloc<float>(P, 3 * (size_t)P.nn);
+    DM_CUDA(cudaMemsetAsync(P.nf_S, 0, sizeof(float) * 3 * (size_t)P.nn, s));  // nodes in no P2P target leaf
     std::vector<int32_t> order(ntiles);
     for (int64_t q = 0; q < ntiles; q++) order[q] = (int32_t)q;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return hng[a] > hng[b]; });
@@ -980,6 +1001,8 @@ void build_near_field(Plan& P) {
                                                     dltile.p + t0, dlrow0.p + t0, P.nf_woff, P.nf_coff, P.nf_ng,
                                                     P.nf_npad, P.nf_cols, P.nf_W);
       DM_LAUNCH("k_nf_pack");
+      k_nf_rowsum<<<(unsigned)(t1 - t0), 128, 0, s>>>(P.p2p_targets + t0, P.cell_range, lcoloff.p, woff, W, P.nf_S);
+      DM_LAUNCH("k_nf_rowsum");
       DM_CUDA(cudaStreamSynchronize(s));
     } else if (mixed) {
       // FP32 copy, [col][node][4] per target leaf (16-byte entries)

@@ -14,6 +14,16 @@
 // together); three MMAs per k-step (hi x hi, hi x lo, lo x hi) accumulate in
 // FP32 in tensor memory.
 //
+// Offset of the states.  The product runs on M - Mbar, Mbar = M of the tile's
+// first column (per state), and the epilogue adds S_i . Mbar with the row sums
+// S_i = sum_j W_ij taken in FP64 at plan time:
+//     u_i = sum_j W_ij . (M_j - Mbar) + S_i . Mbar.
+// For smooth magnetisation the near-field terms of a node cancel to a small
+// residual (a uniform M has no volume charge); M - Mbar is small over a tile,
+// so the rounding of W and M to 16 bits and the tensor core's truncating
+// accumulation act on small terms, and S_i . Mbar carries the large ones in
+// FP32 (S_i itself is the cancelled sum).
+//
 // Data movement.  W is stored at plan time per tile in the order of use:
 // per k-step the BF16 hi rows then the lo rows in the K-major no-swizzle
 // core-matrix layout (8 rows x 16 bytes, the two 8-element halves of a k-step
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
               const int32_t* __restrict__ ngrp,
               const int32_t* __restrict__ npad_t, const int32_t* __restrict__ rownode,
               const int32_t* __restrict__ cols, const unsigned char* __restrict__ W, const float* __restrict__ MP,
-              int64_t nn, int B, float* u, int* err, int debug_no_copies) {
+              const float* __restrict__ S, int64_t nn, int B, int nsb, float* u, int* err, int debug_no_copies) {
   extern __shared__ __align__(1024) unsigned char sm[];
   float* tot = (float*)(sm + (size_t)NF_STAGES * NF_STAGE);  // [row][128 states]
   uint64_t* bars = (uint64_t*)(tot + NF_ROWS * 128);
@@ -99,8 +109,9 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* counts = (int*)(tmem_slot + 2);  // stages issued, stages consumed by the MMA issuer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int sb = blockIdx.x;
-  const int64_t tile = order ? order[blockIdx.y] : blockIdx.y;
+  const int64_t slot_in_grid = blockIdx.x / nsb;  // the state blocks of a tile are neighbours in launch order
+  const int sb = (int)(blockIdx.x - slot_in_grid * nsb);
+  const int64_t tile = order ? order[slot_in_grid] : slot_in_grid;
   const int ng = ngrp[tile];
   if (ng == 0) return;  // uniform over the CTA
   const int npad = npad_t[tile];
@@ -239,6 +250,12 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     const int h = (warp - 4) >> 2, q = warp & 3;
     const int bl = 32 * q + lane, b = sb * 128 + bl;
     const bool live = b < B;
+    float mbar[3];  // M of the tile's first column, this state
+    {
+      const float* m0 = MP + ((int64_t)sb * nn + ct[0]) * 384 + bl;
+#pragma unroll
+      for (int cc = 0; cc < 3; cc++) mbar[cc] = m0[cc * 128];
+    }
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     // this warp's rows of the totals (16-row chunks 2 i + h), zeroed by the warp that adds into them
     for (int c0 = 16 * h; c0 < npad; c0 += 32)
@@ -284,7 +301,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
 #pragma unroll
       for (int k = 0; k < 16; k++)
 #pragma unroll
-        for (int cc = 0; cc < 3; cc++) v[cc][k] = mst[(k * 3 + cc) * 128 + bl];
+        for (int cc = 0; cc < 3; cc++) v[cc][k] = mst[(k * 3 + cc) * 128 + bl] - mbar[cc];
       __syncwarp();
       if (lane == 0) mbar_arrive(sempty(slot));  // this warp has read the stage's M
       const int kl = ks0 + 2;
@@ -323,7 +340,10 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       const int32_t* rn = rownode + tile * NF_ROWS;
       for (int r = h; r < npad; r += 2) {
         const int node = rn[r];
-        if (node >= 0 && live) u[(int64_t)node * B + b] += tot[r * 128 + bl];
+        if (node >= 0 && live) {
+          const float* Si = S + 3ll * node;
+          u[(int64_t)node * B + b] += tot[r * 128 + bl] + (Si[0] * mbar[0] + Si[1] * mbar[1] + Si[2] * mbar[2]);
+        }
       }
     }
   }
@@ -357,7 +377,7 @@ void launch_near_tc(Plan& P, const float* Ms, float* MP, int B, float* u_s, int*
   const unsigned nsb = (unsigned)((B + 127) / 128);
   k_nf_pack_m<<<dim3((unsigned)P.nn, nsb), 128, 0, s>>>(P.nn, B, Ms, MP);
   DM_LAUNCH("k_nf_pack_m");
-  const dim3 grid(nsb, (unsigned)P.nf_ntiles);
+  const dim3 grid((unsigned)(nsb * P.nf_ntiles));
   // launch order: a grid of a few waves starts its largest tiles first (a short
   // tail); a long one runs in Morton order, so that the CTAs in flight gather
   // the M of neighbouring columns from L2 (on GB300 the first is faster on the
@@ -365,9 +385,9 @@ void launch_near_tc(Plan& P, const float* Ms, float* MP, int B, float* u_s, int*
   // 256 states, ~10 waves)
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device);
-  const int32_t* order = (int64_t)grid.x * grid.y < 4ll * nsm ? P.nf_order : nullptr;
+  const int32_t* order = (int64_t)grid.x < 4ll * nsm ? P.nf_order : nullptr;
   k_near_tc<<<grid, NF_THREADS, NF_SMEM, s>>>(order, P.nf_woff, P.nf_coff, P.nf_ng, P.nf_npad, P.nf_rownode, P.nf_cols,
-                                              P.nf_W, MP, P.nn, B, u_s, err, P.debug_flags & 1);
+                                              P.nf_W, MP, P.nf_S, P.nn, B, (int)nsb, u_s, err, P.debug_flags & 1);
   DM_LAUNCH("k_near_tc");
 }
 

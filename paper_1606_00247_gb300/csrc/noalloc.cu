@@ -115,7 +115,7 @@ size_t carve(Plan& P, int B, unsigned char* base, Workspace* W) {
     if (mp) w.MP = c.take<float>(mp);
   }
   if (!mixed || otf) w.u_s = c.take<double>(nn * B);
-  if (otf) w.state = c.take<double>(nt * TET_STATE * B);
+  if (otf) w.state = c.take<double>(nt * TET_STATE * std::min(B, P2P_AT_MIN_B - 1));
   w.err = c.take<int>(1);
   if (W) {
     W->B = w.B;

@@ -1,13 +1,9 @@
-// p2p.cu -- near field (Sec. 2.1): per-tet geometry, per-state records and
-// the FP64 on-the-fly P2P kernel.
+// p2p.cu -- near field (Sec. 2.1): per-tet geometry and the FP64 on-the-fly
+// P2P kernel.
 //
-// P2P kernel layout: one warp per target leaf (blockIdx.x) and state
-// (blockIdx.y).  The source tets of each P2P source leaf are contiguous in
-// sorted tet order; chunks of up to 32 tets (their 66-double geometry records
-// and 56-double state records) are staged in shared memory by TMA bulk copies
-// (cp.async.bulk, completion on an mbarrier).  Lanes take (target node,
-// source tet) pairs; each lane keeps a private partial sum per target node in
-// shared memory and the partials are combined with warp shuffles.
+// The source tets of each P2P source leaf are contiguous in sorted tet order;
+// chunks of up to 32 tets (their 66-double geometry records) are staged in
+// shared memory by bulk copies (cp.async.bulk, completion on an mbarrier).
 #include "common.cuh"
 #include "p2p.cuh"
 
@@ -193,12 +189,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
   return false;
 }
 
-// ---------------------------------------------------------------------------
-// FP64 on-the-fly P2P: one warp per (target leaf, state)
-// ---------------------------------------------------------------------------
 constexpr int P2P_CHUNK = 32;
 
-__global__ void __launch_bounds__(32) k_p2p_fp64(const int32_t* __restrict__ targets, const int4* __restrict__ range,
+// ---------------------------------------------------------------------------
+// FP64 on-the-fly P2P, one state at a time: one warp per (target leaf, state);
+// lanes take (target node, source tet) pairs and contract the pair with the
+// state's per-tet record (pair_contract)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_p2p_fp64_state(const int32_t* __restrict__ targets, const int4* __restrict__ range,
                                                  const int64_t* __restrict__ p2p_off,
                                                  const int32_t* __restrict__ p2p_src,
                                                  const double* __restrict__ nodes_s, const double* __restrict__ geo,
@@ -256,14 +254,155 @@ __global__ void __launch_bounds__(32) k_p2p_fp64(const int32_t* __restrict__ tar
   }
 }
 
-void launch_p2p_fp64(Plan& P, const double* state, int B, double* u_s, int* err, cudaStream_t s) {
-  int64_t nT = (int64_t)P.h_p2p_targets.size();
+// ---------------------------------------------------------------------------
+// FP64 on-the-fly P2P, state-batched: one block of 4 warps per (target leaf,
+// slice of FS states).  The state-independent part of every (target, tet)
+// pair -- the vector a and the symmetric tensor T of the W-form (p2p.cuh) --
+// is computed once and contracted with each state of the slice (16 states):
+//     sum_k M_k . W_k = M(r) . a + (1/2) T : J,   J = dM/dx,  M(r) = M(v0) + J (r - v0).
+// Chunks of 32 source tets: their geometry records are staged by a bulk copy,
+// their per-state M(v0) and J (12 numbers) computed once by the block.  Warp w
+// takes the target nodes w, w + 4, ... of the leaf, lane = tet of the chunk;
+// the 32 lanes' terms are added by a fixed shuffle tree and then, by the
+// warp that owns the target, into its shared-memory sum: no atomics, the
+// result does not depend on timing.
+// ---------------------------------------------------------------------------
+constexpr int PA_FS = 16, PA_WARPS = 4, PA_NT = 64;  // states per block, warps, target nodes per pass
+// dynamic shared memory: geometry records, per-state M(v0) and J of a chunk, per-target sums
+constexpr size_t PA_SMEM = sizeof(double) * (P2P_CHUNK * (TET_GEO + PA_FS * 12) + PA_NT * PA_FS);
+
+__global__ void __launch_bounds__(PA_WARPS * 32) k_p2p_fp64(
+    const int32_t* __restrict__ targets, const int4* __restrict__ range, const int64_t* __restrict__ p2p_off,
+    const int32_t* __restrict__ p2p_src, const double* __restrict__ nodes_s, const int32_t* __restrict__ tets_s,
+    const double* __restrict__ geo, const double* __restrict__ grad, const double* __restrict__ Ms, int B,
+    double* u_s, int* err) {
+  extern __shared__ __align__(128) double pa_smem[];
+  double* s_geo = pa_smem;                                                   // [tet][TET_GEO]
+  double(*s_mj)[PA_FS][12] = (double(*)[PA_FS][12])(pa_smem + P2P_CHUNK * TET_GEO);  // M(v0) (3), J (9)
+  double(*s_sum)[PA_FS] = (double(*)[PA_FS])(pa_smem + P2P_CHUNK * (TET_GEO + PA_FS * 12));
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ bool s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b0 = blockIdx.y * PA_FS;
+  const int32_t T = targets[blockIdx.x];
+  const int4 rT = range[T];
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int32_t i0 = rT.z; i0 < rT.w; i0 += PA_NT) {  // passes of up to PA_NT target nodes
+    const int ntg = min(PA_NT, rT.w - i0);
+    for (int q = tid; q < PA_NT * PA_FS; q += blockDim.x) s_sum[q / PA_FS][q % PA_FS] = 0.0;
+    for (int64_t e = p2p_off[T]; e < p2p_off[T + 1]; e++) {
+      const int4 rS = range[p2p_src[e]];
+      for (int32_t j0 = rS.x; j0 < rS.y; j0 += P2P_CHUNK) {
+        const int ns = min(P2P_CHUNK, rS.y - j0);
+        __syncthreads();  // the previous chunk is no longer read
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const uint32_t bg = (uint32_t)(ns * TET_GEO * sizeof(double));
+          mbar_expect_tx(&bar, bg);
+          tma_bulk_g2s(s_geo, geo + (int64_t)j0 * TET_GEO, bg, &bar);
+        }
+        // per tet and state: M(v0) and J = sum_k M_k (x) grad lambda_k
+        for (int q = tid; q < ns * PA_FS; q += blockDim.x) {
+          const int t = q / PA_FS, f = q - t * PA_FS, b = b0 + f;
+          const int32_t* tv = tets_s + 4ll * (j0 + t);
+          const double* g = grad + 12ll * (j0 + t);
+          double mj[12] = {};
+          if (b < B) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+              const int64_t node = tv[k];
+              const double mx = Ms[(node * 3 + 0) * B + b], my = Ms[(node * 3 + 1) * B + b],
+                           mz = Ms[(node * 3 + 2) * B + b];
+              if (k == 0) {
+                mj[0] = mx;
+                mj[1] = my;
+                mj[2] = mz;
+              }
+              const double m3[3] = {mx, my, mz};
+#pragma unroll
+              for (int x = 0; x < 3; x++)
+#pragma unroll
+                for (int y = 0; y < 3; y++) mj[3 + 3 * x + y] += m3[x] * g[3 * k + y];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 12; c++) s_mj[t][f][c] = mj[c];
+        }
+        if (tid == 0) {
+          const bool ok = mbar_wait_bounded(&bar, phase);
+          if (!ok) {
+            atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+            mbar_wait_bounded(&bar, phase);  // let the copy in flight land before leaving
+          }
+          s_ok = ok;
+        }
+        phase ^= 1;
+        __syncthreads();  // s_geo landed (seen by thread 0), s_mj complete
+        if (!s_ok) return;  // the whole block leaves together
+        for (int i = warp; i < ntg; i += PA_WARPS) {
+          const double* r = nodes_s + 3ll * (i0 + i);
+          double acc[PA_FS];
+#pragma unroll
+          for (int f = 0; f < PA_FS; f++) acc[f] = 0.0;
+          if (lane < ns) {
+            const double* G = s_geo + lane * TET_GEO;
+            PairAT at;
+            pair_at(G, r[0], r[1], r[2], at);
+            const double d0 = r[0] - G[0], d1 = r[1] - G[1], d2 = r[2] - G[2];
+#pragma unroll
+            for (int f = 0; f < PA_FS; f++) {
+              const double* mj = s_mj[lane][f];
+              const double* J = mj + 3;
+              const double Mr0 = mj[0] + J[0] * d0 + J[1] * d1 + J[2] * d2;
+              const double Mr1 = mj[1] + J[3] * d0 + J[4] * d1 + J[5] * d2;
+              const double Mr2 = mj[2] + J[6] * d0 + J[7] * d1 + J[8] * d2;
+              const double TJ = at.T[0] * J[0] + at.T[1] * J[4] + at.T[2] * J[8] + at.T[3] * (J[1] + J[3]) +
+                                at.T[4] * (J[2] + J[6]) + at.T[5] * (J[5] + J[7]);
+              acc[f] = Mr0 * at.a[0] + Mr1 * at.a[1] + Mr2 * at.a[2] + 0.5 * TJ;
+            }
+          }
+#pragma unroll
+          for (int f = 0; f < PA_FS; f++) {
+            double v = acc[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_sum[i][f] += v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < ntg * PA_FS; q += blockDim.x) {
+      const int i = q / PA_FS, f = q - i * PA_FS;
+      if (b0 + f < B) u_s[(int64_t)(i0 + i) * B + b0 + f] += s_sum[i][f] * (1.0 / (4.0 * M_PI));
+    }
+    __syncthreads();  // s_sum is read before the next pass clears it
+  }
+}
+
+void launch_p2p_fp64(Plan& P, const double* Ms, const double* state, int B, double* u_s, int* err, cudaStream_t s) {
+  const int64_t nT = (int64_t)P.h_p2p_targets.size();
   if (nT == 0) return;
-  static_assert(sizeof(double) * P2P_CHUNK * TET_GEO % 16 == 0, "TMA size");
-  dim3 grid((unsigned)nT, B);
-  k_p2p_fp64<<<grid, 32, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s, P.tet_geo, state,
-                                 P.nt, B, u_s, err);
+  static_assert(sizeof(double) * TET_GEO % 16 == 0 && sizeof(double) * TET_STATE % 16 == 0,
+                "bulk copies of whole records");
+  if (B < P2P_AT_MIN_B) {
+    k_p2p_fp64_state<<<dim3((unsigned)nT, B), 32, 0, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src,
+                                                          P.nodes_s, P.tet_geo, state, P.nt, B, u_s, err);
+    DM_LAUNCH("k_p2p_fp64_state");
+    return;
+  }
+  static bool attr = false;
+  if (!attr) {
+    DM_CUDA(cudaFuncSetAttribute(k_p2p_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
+    attr = true;
+  }
+  const dim3 grid((unsigned)nT, (unsigned)((B + PA_FS - 1) / PA_FS));
+  k_p2p_fp64<<<grid, PA_WARPS * 32, PA_SMEM, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s,
+                                             P.tets_s, P.tet_geo, P.tet_grad, Ms, B, u_s, err);
   DM_LAUNCH("k_p2p_fp64");
 }
+
 
 }  // namespace demag

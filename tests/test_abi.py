@@ -43,9 +43,9 @@ def test_options_default_and_status_strings(lib):
     o = _lib.demag_options_default()
     assert (o.p, o.leaf_size, o.theta, o.precision, o.near_mode, o.max_batch, o.autotune) == (4, 32, 0.5, 0, 0, 1, 0)
     assert (o.profile, o.m2l_targets_per_cta, o.m2l_kps, o.m2l_promote, o.m2l_promote_rows,
-            o.m2l_table_batch, o.sources, o.near_tc, o.graph) == (0,) * 9
+            o.m2l_table_batch, o.sources, o.near_tc, o.graph, o.m2l_split_degree) == (0,) * 10
     # the binding's struct matches the library's: the default fills exactly sizeof(demag_options)
-    assert ctypes.sizeof(_lib.demag_options) == 15 * 4 + 8 + 4  # fifteen ints, one double, tail padding
+    assert ctypes.sizeof(_lib.demag_options) == 16 * 4 + 8  # sixteen ints, one double
     for s in range(7):
         assert _lib.demag_status_string(s)
     assert _lib.demag_status_string(99) == "unknown status"

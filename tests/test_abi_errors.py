@@ -38,7 +38,7 @@ def _create(mesh, p=4, leaf=8, theta=0.5, **opts):
     (dict(near_mode=2), INVALID), (dict(precision=5), INVALID), (dict(m2l_targets_per_cta=3), INVALID),
     (dict(m2l_kps=9), INVALID), (dict(m2l_promote_rows=65), INVALID), (dict(sources=3), INVALID),
     (dict(sources=1, near_mode=0), UNSUPPORTED), (dict(sources=2, near_mode=0), UNSUPPORTED),
-    (dict(graph=2), INVALID),
+    (dict(graph=2), INVALID), (dict(m2l_split_degree=1), INVALID),
 ])
 def test_plan_create_rejects(mesh, kw, status):
     assert _create(mesh, **kw) == status

@@ -84,11 +84,14 @@ def test_noalloc_rejects_oversized_scratch_and_host_pointers():
     from paper_1606_00247_gb300.api import Plan
 
     nodes, tets = inputs.sphere(h=0.12)
-    # on-the-fly near field: 56 doubles per tet and state -> far beyond 64 MiB for 16 states
-    plan = Plan(nodes, tets, p=4, leaf_size=32, max_batch=16, near_mode=0)
-    M = torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], batch=16), device="cuda")
-    u = torch.empty((16, nodes.shape[0]), dtype=torch.float64, device="cuda")
-    H = torch.empty((16, nodes.shape[0], 3), dtype=torch.float64, device="cuda")
+    # FP64 moments and locals: 2 x 165 doubles per cell and state at p = 8 -> far beyond
+    # 64 MiB for 64 states
+    B = 64
+    plan = Plan(nodes, tets, p=8, leaf_size=8, max_batch=B, near_mode=0)
+    assert plan.stats()["n_cells"] * 165 * 16 * B > 64 * 2**20
+    M = torch.as_tensor(inputs.gaussian_unit_m(nodes.shape[0], batch=B), device="cuda")
+    u = torch.empty((B, nodes.shape[0]), dtype=torch.float64, device="cuda")
+    H = torch.empty((B, nodes.shape[0], 3), dtype=torch.float64, device="cuda")
     st = _call_noalloc(plan, M, u, H)
     assert st == _lib.DEMAG_ERR_INVALID_ARG
     assert "fixed area holds" in _lib.demag_last_error()
