@@ -571,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "n_tets": st0["n_tets"], "n_nodes": st0["n_nodes"],
                    "p": w["p"], "theta": w["theta"], "leaf_size": w["leaf"], "batch_per_gpu": B,
                    "precision": args.precision, "near_mode": args.near_mode, "l2": "flushed between steps",
-                   "sources": args.sources, "m2l_split_degree": ("p-4" if args.m2l_split_degree == 0 else "all"),
+                   "sources": args.sources, "m2l_split_degree": ("default" if args.m2l_split_degree == 0 else "all"),
                    "parallelism": f"replicas x{world}", "n_cells": st0["n_cells"], "n_m2l": st0["n_m2l"],
                    "n_p2p_leaf_pairs": st0["n_p2p"], "n_p2p_pairs": st0["n_p2p_pairs"],
                    "plan_ms": st0["plan_ms"], "m2l_operators": st0["n_m2l_ops"],

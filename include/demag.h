@@ -148,8 +148,8 @@ typedef struct {
   int m2l_split_degree; /* DEMAG_MIXED_BF16X3, tensor-core M2L: 0 (default)
                           forms the products with the second BF16 limb
                           (hi x lo, lo x hi) only for the terms of degree
-                          |m| + |n| <= p - 4 of the translation (Sec. 2.3);
-                          the four highest degrees, whose share of the
+                          |m| + |n| <= p - 4 of the translation (Sec. 2.3;
+                          p - 3 for p < 8); the highest degrees, whose share of the
                           expansion falls off like a power of the cell
                           size over the distance, take hi x hi alone
                           (about half the MMAs); < 0: both products for

@@ -130,7 +130,8 @@ __host__ __device__ constexpr int degree_of(int m) {
 //               k-steps with no such rows keep one limb and one MMA.
 constexpr int TC_LS_ALL2 = 0, TC_LS_ALL3 = 99;
 // default split degree: p - TC_SD_BELOW (the four highest term degrees of the
-// expansion take hi x hi alone)
+// expansion take hi x hi alone) from p = 8 on, p - 3 for lower orders (whose
+// highest degrees carry a larger share)
 constexpr int TC_SD_BELOW = 4;
 
 __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int ls) {
@@ -186,7 +187,7 @@ __host__ __device__ constexpr TcLayout tc_layout(int p, bool bf16, int ls) {
 // the default split degree of the order and with two limbs on every k-step
 // (DEMAG_MIXED_BF16X3), and with three limbs (DEMAG_MIXED_BF16X6)
 constexpr bool tc_order(int p) { return p == 4 || p == 6 || p == 8 || p == 10; }
-__host__ __device__ constexpr int tc_split_degree(int p) { return p - TC_SD_BELOW; }
+__host__ __device__ constexpr int tc_split_degree(int p) { return p >= 8 ? p - TC_SD_BELOW : p - 3; }
 
 // launch shape: `nt` targets per CTA sharing each source's moments, `kps`
 // k-steps of one source per ring slot (A slices, then one K region per target)

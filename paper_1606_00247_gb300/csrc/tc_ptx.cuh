@@ -110,6 +110,11 @@ static __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* 
       "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
       : "memory");
 }
+static __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
+}
 static __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 static __device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
@@ -121,13 +126,14 @@ static __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t nco
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// split of 16 FP32 values into BF16 hi (round to nearest) and BF16 lo (the
+// split of N FP32 values into BF16 hi (round to nearest) and BF16 lo (the
 // rounding of the residual, exact in FP32), packed two per 32-bit word with the
 // even element in the low half (the order of the K elements in a tensor-memory
 // row)
-static __device__ __forceinline__ void split_bf16x16(const float* v, uint32_t* hi, uint32_t* lo) {
+template <int N>  // N values -> N / 2 packed pairs of each limb
+static __device__ __forceinline__ void split_bf16(const float* v, uint32_t* hi, uint32_t* lo) {
 #pragma unroll
-  for (int u = 0; u < 8; u++) {
+  for (int u = 0; u < N / 2; u++) {
     uint32_t h;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(v[2 * u + 1]), "f"(v[2 * u]));
     const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);

@@ -113,3 +113,33 @@ def test_near_tc_dipole_sources(orc):
     u, _ = _plan(nodes, tets, precision="bf16x3", **kw).eval(M)
     ref = orc.dipole_direct(nodes, tets, M[0])
     assert rel_l2(u[0].cpu().numpy(), ref) < 3e-5
+
+
+@pytest.mark.parametrize("B", [2, 160])
+def test_near_tc_repeated_evaluations_are_identical(B):
+    """One plan evaluated five times: every evaluation gives the same bits and
+    no device wait expires.  The state warps take part in every column group,
+    so each waits for every use of each shared-memory stage in order (a
+    skipped use lets a phase parity alias an older phase).  A thin film with
+    smooth domains (long tiles) and a ball with one full and one partial
+    state block."""
+    from paper_1606_00247_gb300 import _lib
+
+    if B == 2:
+        nodes, tets = inputs.thin_film(nx=288, ny=144, nz=2, size=(1000.0, 500.0, 10.0))
+        M = np.stack([inputs.landau_m(nodes, size=(1000.0, 500.0)),
+                      inputs.landau_m(nodes, size=(1000.0, 500.0), seed=inputs.MAG_SEED + 7)])
+        kw = dict(p=8, leaf_size=128)
+    else:
+        nodes, tets = inputs.sphere(h=0.06)
+        M = inputs.smoothed_unit_m(tets, nodes.shape[0], batch=B, seed=405)
+        kw = dict(p=6, leaf_size=64)
+    pl = _plan(nodes, tets, theta=0.5, near_mode=1, max_batch=B, precision="bf16x3", **kw)
+    assert pl.stats()["n_near_tiles"] > 0
+    Md = torch.as_tensor(M, device="cuda")
+    u0, H0 = pl.eval(Md)
+    for _ in range(4):
+        u, H = pl.eval(Md)
+        st = _lib.demag_eval_status(pl.handle, torch.cuda.current_stream().cuda_stream)
+        assert st == _lib.DEMAG_OK
+        assert torch.equal(u, u0) and torch.equal(H, H0)
