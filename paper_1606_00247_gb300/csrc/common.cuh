@@ -139,6 +139,8 @@ struct Plan {
 
   // targets
   int32_t* node_leaf = nullptr;     // sorted node -> leaf cell
+  int32_t* node_leaves = nullptr;   // leaves holding nodes (their nodes are cell_range[c].z .. .w)
+  int64_t n_node_leaves = 0;
   // source leaves: support nodes (unique nodes of the leaf's tets)
   int64_t n_sup = 0;
   int64_t* sup_off = nullptr;       // ncells + 1

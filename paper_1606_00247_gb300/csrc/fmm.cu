@@ -52,12 +52,15 @@ __device__ __forceinline__ void scaled_monomials(int p, int nc, const unsigned c
 // input / output layout
 // ---------------------------------------------------------------------------
 // Ms[(i*3+c)*B + b] = M[(b*nn + perm[i])*3 + c]
-__global__ void k_gather_M(int64_t nn, int B, const int32_t* __restrict__ perm, const double* __restrict__ M, double* Ms) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nn) return;
-  int64_t g = perm[i];
-  for (int b = 0; b < B; b++)
-    for (int c = 0; c < 3; c++) Ms[(i * 3 + c) * B + b] = M[((int64_t)b * nn + g) * 3 + c];
+// block per (sorted node, 128 states), thread = state: stores coalesce over states
+__global__ void __launch_bounds__(128) k_gather_M(int64_t nn, int B, const int32_t* __restrict__ perm,
+                                                  const double* __restrict__ M, double* Ms) {
+  const int64_t i = blockIdx.x;
+  const int b = blockIdx.y * 128 + threadIdx.x;
+  if (b >= B) return;
+  const int64_t g = perm[i];
+#pragma unroll
+  for (int c = 0; c < 3; c++) Ms[(i * 3 + c) * B + b] = M[((int64_t)b * nn + g) * 3 + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -359,7 +362,7 @@ void eval_fp64_ws(Plan& P, Workspace& W, const double* M, int B, double* u, doub
   const int p = P.p, nc = P.nc;
   StageClock clk(P, s, profile_ok);
   clk.begin(DEMAG_STAGE_GATHER);
-  k_gather_M<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms);
+  k_gather_M<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms);
   DM_LAUNCH("k_gather_M");
   clk.launched();
   clk.end();
@@ -441,7 +444,7 @@ void near_field_fp64(Plan& P, Workspace& W, int B, StageClock& clk, cudaStream_t
 }
 
 void launch_gather_M(Plan& P, const double* M, int B, double* Ms, cudaStream_t s) {
-  k_gather_M<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, M, Ms);
+  k_gather_M<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.nn, B, P.node_perm, M, Ms);
   DM_LAUNCH("k_gather_M");
 }
 

@@ -27,17 +27,23 @@ static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t > 0 ? (n
 
 namespace {
 
-__global__ void k_gather_M32(int64_t nn, int B, const int32_t* __restrict__ perm, const double* __restrict__ M,
-                             float* Ms, double* Ms64) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nn) return;
-  int64_t g = perm[i];
-  for (int b = 0; b < B; b++)
-    for (int c = 0; c < 3; c++) {
-      double v = M[((int64_t)b * nn + g) * 3 + c];
-      Ms[(i * 3 + c) * B + b] = (float)v;
-      if (Ms64) Ms64[(i * 3 + c) * B + b] = v;
-    }
+// M (state, original node, component) -> Ms (sorted node, component, state):
+// block per (sorted node, 128 states), thread = state, so the stores coalesce
+// over the states; each thread reads the 24 contiguous bytes of its state's
+// (node, x y z) row
+__global__ void __launch_bounds__(128) k_gather_M32(int64_t nn, int B, const int32_t* __restrict__ perm,
+                                                    const double* __restrict__ M, float* Ms, double* Ms64) {
+  const int64_t i = blockIdx.x;
+  const int b = blockIdx.y * 128 + threadIdx.x;
+  if (b >= B) return;
+  const int64_t g = perm[i];
+  const double* src = M + ((int64_t)b * nn + g) * 3;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const double v = src[c];
+    Ms[(i * 3 + c) * B + b] = (float)v;
+    if (Ms64) Ms64[(i * 3 + c) * B + b] = v;
+  }
 }
 
 __global__ void k_ghat32(const int32_t* __restrict__ leaves, const int32_t* __restrict__ level,
@@ -53,25 +59,36 @@ __global__ void k_ghat32(const int32_t* __restrict__ leaves, const int32_t* __re
     }
 }
 
-// P2M: one block per (source leaf, 16 coefficients n, 128 states), thread =
-// state.  For 16 support nodes at a time the block gathers, per node, the 48
-// values Gt[n - e_c] its 16 coefficients need (0 where n_c = 0) into shared
-// memory in the order of use, so one node costs 12 broadcast 16-byte reads for
-// 48 FMAs; M of the next node is loaded while the current one is applied.
-constexpr int P2M_NN = 16, P2M_NE = 16, P2M_B = 128;
+// P2M: one block per (source leaf, 56 coefficients n, 128 states), thread =
+// state (three blocks per leaf at p = 8).  Support nodes come in chunks of 16,
+// double-buffered in shared memory by asynchronous copies (cp.async), the
+// next chunk in flight while the current one is applied: per node the 168
+// values Gt[n - e_c] the block's 56 coefficients need (0 where n_c = 0), in
+// the order of use, and M of the 128 states.  One node costs 42 broadcast
+// 16-byte reads of Gt and 3 reads of M for 168 FMAs.
+constexpr int P2M_NN = 56, P2M_NE = 16, P2M_B = 128;
+constexpr size_t P2M_SMEM = sizeof(float) * 2 * P2M_NE * (P2M_NN * 3 + 3 * P2M_B);  // two chunk buffers
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
 
 __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ leaves,
                                                  const int64_t* __restrict__ sup_off,
                                                  const int32_t* __restrict__ sup_node, const float* __restrict__ G,
                                                  const float* __restrict__ Ms, int nc, int nc1, int B, float* Q) {
-  __shared__ __align__(16) float sG[P2M_NE][P2M_NN * 3];
+  extern __shared__ __align__(16) float p2m_smem[];
+  float(*sG)[P2M_NE][P2M_NN * 3] = (float(*)[P2M_NE][P2M_NN * 3])p2m_smem;               // [2][node][(j, c)]
+  float(*sM)[P2M_NE][3][P2M_B] = (float(*)[P2M_NE][3][P2M_B])(p2m_smem + 2 * P2M_NE * P2M_NN * 3);  // [2][node][c][state]
   __shared__ int six[P2M_NN * 3];
   const int32_t c = leaves[blockIdx.x];
   const int n0 = blockIdx.y * P2M_NN;
-  const int b = blockIdx.z * P2M_B + threadIdx.x;
+  const int tid = threadIdx.x, b = blockIdx.z * P2M_B + tid;
   const bool live = b < B;
-  if (threadIdx.x < P2M_NN * 3) {
-    const int j = threadIdx.x / 3, comp = threadIdx.x - 3 * j;
+  for (int t = tid; t < P2M_NN * 3; t += blockDim.x) {
+    const int j = t / 3, comp = t - 3 * j;
     int na = 0, nb = 0, nz = 0, ix = -1;
     if (n0 + j < nc) {
       mi_decode(n0 + j, na, nb, nz);
@@ -79,48 +96,55 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
       if (comp == 1 && nb) ix = mi_index(na, nb - 1, nz);
       if (comp == 2 && nz) ix = mi_index(na, nb, nz - 1);
     }
-    six[threadIdx.x] = ix;
+    six[t] = ix;
   }
+  __syncthreads();
+  const int64_t so = sup_off[c], eo = sup_off[c + 1];
+  auto stage = [&](int64_t e0, int buf) {  // one chunk of support nodes into buffer buf
+    const int ne = (int)min((int64_t)P2M_NE, eo - e0);
+    for (int q = tid; q < P2M_NE * P2M_NN * 3; q += blockDim.x) {
+      const int r = q / (P2M_NN * 3), jc = q - r * (P2M_NN * 3);
+      const int ix = six[jc];
+      const bool ok = r < ne && ix >= 0;
+      cp_async4(&sG[buf][r][jc], ok ? G + (e0 + r) * nc1 + ix : G, ok);
+    }
+    for (int r = 0; r < P2M_NE; r++) {
+      const bool ok = r < ne && live;
+      const float* mp = Ms + (ok ? (int64_t)sup_node[e0 + r] * 3 * B + b : 0);
+#pragma unroll
+      for (int cc = 0; cc < 3; cc++) cp_async4(&sM[buf][r][cc][tid], ok ? mp + (int64_t)cc * B : Ms, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   float acc[P2M_NN];
 #pragma unroll
   for (int j = 0; j < P2M_NN; j++) acc[j] = 0.f;
-  const int64_t so = sup_off[c], eo = sup_off[c + 1];
-  for (int64_t e0 = so; e0 < eo; e0 += P2M_NE) {
+  if (so < eo) stage(so, 0);
+  int buf = 0;
+  for (int64_t e0 = so; e0 < eo; e0 += P2M_NE, buf ^= 1) {
     const int ne = (int)min((int64_t)P2M_NE, eo - e0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < ne * P2M_NN * 3; q += blockDim.x) {
-      const int r = q / (P2M_NN * 3), jc = q - r * (P2M_NN * 3);
-      const int ix = six[jc];
-      sG[r][jc] = ix >= 0 ? G[(e0 + r) * nc1 + ix] : 0.f;
+    if (e0 + P2M_NE < eo) {
+      stage(e0 + P2M_NE, buf ^ 1);  // the other buffer was released by the barrier that ended the last chunk
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    __syncthreads();
-    if (live) {
-      const float* mp = Ms + (int64_t)sup_node[e0] * 3 * B + b;
-      float m0 = mp[0], m1 = mp[B], m2 = mp[2 * B];
-      for (int r = 0; r < ne; r++) {
-        float n0v = 0.f, n1v = 0.f, n2v = 0.f;
-        if (r + 1 < ne) {
-          const float* np = Ms + (int64_t)sup_node[e0 + r + 1] * 3 * B + b;
-          n0v = np[0];
-          n1v = np[B];
-          n2v = np[2 * B];
-        }
-        const float4* g4 = (const float4*)sG[r];
+    __syncthreads();  // this chunk complete in shared memory for every thread
+    for (int r = 0; r < ne; r++) {
+      const float m0 = sM[buf][r][0][tid], m1 = sM[buf][r][1][tid], m2 = sM[buf][r][2][tid];
+      const float4* g4 = (const float4*)sG[buf][r];
 #pragma unroll
-        for (int q = 0; q < P2M_NN * 3 / 4; q++) {
-          const float4 g = g4[q];  // values 4q .. 4q+3 = (j, comp) pairs in order
-          const float gv[4] = {g.x, g.y, g.z, g.w};
+      for (int q = 0; q < P2M_NN * 3 / 4; q++) {
+        const float4 g = g4[q];  // values 4q .. 4q+3 = (j, comp) pairs in order
+        const float gv[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const int jc = 4 * q + u, j = jc / 3, comp = jc % 3;
-            acc[j] = fmaf(gv[u], comp == 0 ? m0 : (comp == 1 ? m1 : m2), acc[j]);
-          }
+        for (int u = 0; u < 4; u++) {
+          const int jc = 4 * q + u, j = jc / 3, comp = jc % 3;
+          acc[j] = fmaf(gv[u], comp == 0 ? m0 : (comp == 1 ? m1 : m2), acc[j]);
         }
-        m0 = n0v;
-        m1 = n1v;
-        m2 = n2v;
       }
     }
+    __syncthreads();  // the buffer may be refilled
   }
   if (live)
 #pragma unroll
@@ -191,8 +215,9 @@ __global__ void k_l2l32(const int32_t* __restrict__ parents, int64_t npar, const
     }
 }
 
-// L2P: block per (node, 128 states); the node's monomials s_m(z/s) are formed
-// once in shared memory, then thread = state: u = sum_m Lt_m s_m (coalesced L)
+// L2P, node-wise (orders whose leaf-wise tile exceeds shared memory): block
+// per (node, 128 states); the node's monomials s_m(z/s) are formed once in
+// shared memory, then thread = state: u = sum_m Lt_m s_m (coalesced L)
 __global__ void __launch_bounds__(128) k_l2p32(const int32_t* __restrict__ node_leaf, const int32_t* __restrict__ level,
                                                const double* __restrict__ nodes_s, const double* __restrict__ centre,
                                                double side, int nc, int B, const float* __restrict__ L, float* u) {
@@ -223,6 +248,101 @@ __global__ void __launch_bounds__(128) k_l2p32(const int32_t* __restrict__ node_
   }
   if (m < nc) v0 = fmaf(Lc[(int64_t)m * B], sm_[m], v0);
   u[i * B + b] = v0 + v1;
+}
+
+// L2P, leaf-wise: block per (leaf holding nodes, 128 states).  The leaf's local
+// expansion (nc coefficients x 128 states, 84 KB at p = 8) is staged once in
+// shared memory (coalesced over states); the nodes follow in chunks of 16:
+// their monomials s_m(z/s) are formed in shared memory ([m][16 nodes]), and
+// thread = state accumulates the 16 potentials in registers, each coefficient
+// read once per chunk and each monomial row a broadcast float4 load.
+constexpr int L2P_NCH = 16;
+
+__global__ void __launch_bounds__(128) k_l2p32_leaf(const int32_t* __restrict__ leaves, const int4* __restrict__ range,
+                                                    const int32_t* __restrict__ level,
+                                                    const double* __restrict__ nodes_s,
+                                                    const double* __restrict__ centre, double side, int nc, int B,
+                                                    const float* __restrict__ L, float* u) {
+  extern __shared__ __align__(16) float l2p_smem[];
+  float* sL = l2p_smem;                                // [m][128 states]
+  float4* smono = (float4*)(l2p_smem + nc * 128);      // [m][16 nodes] as 4 float4
+  const int32_t c = leaves[blockIdx.x];
+  const int4 r = range[c];
+  const int tid = threadIdx.x, b = blockIdx.y * 128 + tid;
+  const bool live = b < B;
+  // the tile by asynchronous 4-byte copies, all in flight at once (zero fill
+  // for states beyond B)
+  const float* Lc = L + (int64_t)c * nc * B + (live ? b : 0);
+  for (int m = 0; m < nc; m++)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                     sL + m * 128 + tid)),
+                 "l"(Lc + (int64_t)m * B), "r"(live ? 4 : 0)
+                 : "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  const double inv_s = 1.0 / ldexp(side, -level[c]);
+  float* sm = (float*)smono;
+  for (int32_t i0 = r.z; i0 < r.w; i0 += L2P_NCH) {
+    const int nk = min(L2P_NCH, r.w - i0);
+    __syncthreads();  // sL complete (first chunk); the previous chunk's monomials are read
+    // monomials: thread t forms those of node t % 16 for m = t / 16, t / 16 + 8, ...
+    {
+      const int k = tid & (L2P_NCH - 1);
+      float z[3] = {0.f, 0.f, 0.f};
+      if (k < nk) {
+        const int64_t i = i0 + k;
+#pragma unroll
+        for (int a = 0; a < 3; a++) z[a] = (float)((nodes_s[3 * i + a] - centre[3 * c + a]) * inv_s);
+      }
+      for (int m = tid / L2P_NCH; m < nc; m += 128 / L2P_NCH) {
+        int e[3];
+        mi_decode(m, e[0], e[1], e[2]);
+        float v = 1.f;
+        for (int a = 0; a < 3; a++)
+          for (int q = 1; q <= e[a]; q++) v = v * z[a] / q;
+        sm[m * L2P_NCH + k] = v;
+      }
+    }
+    __syncthreads();
+    float acc[L2P_NCH];
+#pragma unroll
+    for (int k = 0; k < L2P_NCH; k++) acc[k] = 0.f;
+    for (int m = 0; m < nc; m++) {
+      const float l = sL[m * 128 + tid];
+#pragma unroll
+      for (int q = 0; q < L2P_NCH / 4; q++) {
+        const float4 w = smono[m * (L2P_NCH / 4) + q];
+        acc[4 * q] = fmaf(l, w.x, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(l, w.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(l, w.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(l, w.w, acc[4 * q + 3]);
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < L2P_NCH; k++)
+        if (k < nk) u[(int64_t)(i0 + k) * B + b] = acc[k];
+    }
+  }
+}
+
+void launch_l2p32(Plan& P, int B, const float* L, float* u, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)P.nc * (128 + L2P_NCH);
+  if (smem > 227 * 1024) {  // p = 12: the node-wise kernel
+    k_l2p32<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.node_leaf, P.cell_level, P.nodes_s,
+                                                                               P.cell_centre, P.side, P.nc, B, L, u);
+    DM_LAUNCH("k_l2p32");
+    return;
+  }
+  if (P.n_node_leaves == 0) return;
+  static size_t attr = 0;
+  if (smem > attr) {
+    DM_CUDA(cudaFuncSetAttribute(k_l2p32_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const dim3 grid((unsigned)P.n_node_leaves, (unsigned)((B + 127) / 128));
+  k_l2p32_leaf<<<grid, 128, smem, s>>>(P.node_leaves, P.cell_range, P.cell_level, P.nodes_s, P.cell_centre, P.side,
+                                       P.nc, B, L, u);
+  DM_LAUNCH("k_l2p32_leaf");
 }
 
 // u and the mass-lumped H of the mixed path, in the caller's layout: tiles of
@@ -441,7 +561,8 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   const int nc = P.nc;
   StageClock clk(P, s, profile_ok);
   clk.begin(DEMAG_STAGE_GATHER);
-  k_gather_M32<<<nblk(P.nn, 128), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms32, otf ? W.Ms : nullptr);
+  k_gather_M32<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.nn, B, P.node_perm, Md, W.Ms32,
+                                                                                 otf ? W.Ms : nullptr);
   DM_LAUNCH("k_gather_M32");
   clk.launched();
   clk.end();
@@ -450,7 +571,13 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   if (!P.h_src_leaves.empty()) {
     dim3 grid((unsigned)P.h_src_leaves.size(), (unsigned)((nc + P2M_NN - 1) / P2M_NN),
               (unsigned)((B + P2M_B - 1) / P2M_B));
-    k_p2m32<<<grid, P2M_B, 0, s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1, B, W.Q32);
+    static bool attr = false;
+    if (!attr) {
+      DM_CUDA(cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2M_SMEM));
+      attr = true;
+    }
+    k_p2m32<<<grid, P2M_B, P2M_SMEM, s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1, B,
+                                           W.Q32);
     DM_LAUNCH("k_p2m32");
     clk.launched();
   }
@@ -490,9 +617,7 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   }
   clk.end();
   clk.begin(DEMAG_STAGE_L2P);
-  k_l2p32<<<dim3((unsigned)P.nn, (unsigned)((B + 127) / 128)), 128, 0, s>>>(P.node_leaf, P.cell_level, P.nodes_s,
-                                                                             P.cell_centre, P.side, nc, B, W.L32, W.u32);
-  DM_LAUNCH("k_l2p32");
+  launch_l2p32(P, B, W.L32, W.u32, s);
   clk.launched();
   clk.end();
   if (otf) {

@@ -28,13 +28,13 @@
 // per k-step the BF16 hi rows then the lo rows in the K-major no-swizzle
 // core-matrix layout (8 rows x 16 bytes, the two 8-element halves of a k-step
 // 128 bytes apart, 8-row groups 256 bytes apart), so one bulk copy per stage
-// of three k-steps (one column group) fills a slot of a six-slot shared-memory
-// ring.  The A operand never touches shared memory: the warps that own the
-// states load M of the group's 16 columns from L2 into registers one group
-// ahead (coalesced over states: M is stored state-innermost), split it into
-// hi and lo and write it straight into a ring of tensor-memory slots
-// (tcgen05.st), from which the MMA reads it.  One thread
-// streams W, one thread issues the MMAs and frees the slots with
+// of three k-steps (one column group) fills a shared-memory ring slot; the M
+// of the group's 16 columns (FP32, states innermost, 1.5 KB each) comes with
+// it.  The A operand itself never touches shared memory: the warps that own
+// the states read their M from the stage, split it into hi and lo and write it
+// straight into a ring of tensor-memory slots (tcgen05.st), from which the MMA
+// reads it.  One thread streams the stages, one thread issues the MMAs and
+// frees the slots with
 // tcgen05.commit; the state warps move finished accumulators into FP32 totals
 // (below) and at the end add the totals to u (rows are distinct nodes: no
 // atomics).
@@ -54,8 +54,9 @@ using namespace tcx;
 constexpr int NF_RING = 16;                      // A slots in tensor memory (k-steps in flight)
 constexpr int NF_KSTEP_MAX = 64 * NF_ROWS;       // W bytes of one k-step: 2 limbs x 128 rows x 32 B
 constexpr int NF_WPART = 3 * NF_KSTEP_MAX;       // W of one column group (x, y, z k-steps): 24 KB
-constexpr int NF_STAGE = NF_WPART;               // ring slot: W of one column group, 24 KB
-constexpr int NF_STAGES = 6;
+constexpr int NF_MCOL = 3 * 128 * 4;             // M of one column for one state block: 1,536 B
+constexpr int NF_STAGE = NF_WPART + 16 * NF_MCOL;  // ring slot: W and M of one column group, 48 KB
+constexpr int NF_STAGES = 3;
 constexpr int NF_CHUNK = 24;                     // k-steps per accumulator before it is promoted
 constexpr int NF_PROMOTE_AT = 8;                 // ... promoted after this many k-steps of the next chunk
 constexpr int NF_THREADS = 384;                  // 4 control warps + 2 x 4 state warps
@@ -80,7 +81,8 @@ __global__ void k_nf_pack_m(int64_t nn, int B, const float* __restrict__ Ms, flo
 // One CTA per (128-state block, tile); the state blocks of a tile are
 // neighbours in launch order so the second reads the tile's W from L2.
 //   warp 0       producer: per column group one stage = the group's W (one
-//                bulk copy)
+//                bulk copy) and the M of its 16 columns (one bulk copy each,
+//                issued by lanes 0..15)
 //   warp 1       MMA issuer
 //   warp 2       tensor-memory allocation
 //   warps 4..11  state warps: warp 4 + 4 h + q owns tensor-memory lanes
@@ -88,7 +90,7 @@ __global__ void k_nf_pack_m(int64_t nn, int B, const float* __restrict__ Ms, flo
 //                8h .. 8h + 7 of every column group from shared memory into
 //                the A ring of tensor memory (split BF16).
 // A stage is free again when the MMAs of its three k-steps are done (one
-// tcgen05.commit).
+// tcgen05.commit) and the eight state warps that read its M have arrived.
 // Accumulation.  The tensor core adds each MMA's products into its FP32
 // accumulator aligned to the larger operand, so its error grows with the
 // number of MMAs an accumulator takes.  Every NF_CHUNK k-steps the issuer
@@ -127,10 +129,10 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
   if (tid == 0) {
     for (int i = 0; i < NF_STAGES; i++) {
       mbar_init(sfull(i), 1);
-      mbar_init(sempty(i), 1);  // the MMA commit after the group's last k-step
+      mbar_init(sempty(i), 1 + 8);  // the MMA commit and the four state warps that read its M
     }
     for (int i = 0; i < NF_RING; i++) {
-      mbar_init(afull(i), 8);  // the eight state warps, each filling its lanes and half of the columns
+      mbar_init(afull(i), 8);  // the four warps of the half that fills the slot
       mbar_init(aempty(i), 1);
     }
     for (int i = 0; i < 2; i++) {
@@ -151,20 +153,36 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
   const int32_t* ct = cols + coff[tile];
 
   if (warp == 0) {
-    // ---- producer: one stage (the group's W, one bulk copy) per column group
+    // ---- producer (whole warp): one stage per column group
+    const unsigned char* Wt = W + woff[tile];
+    const float* MPb = MP + (int64_t)sb * nn * 384;
     int g = 0;
-    if (lane == 0 && !debug_no_copies) {  // test hook: no stage is ever filled, so the waits for them expire
-      const unsigned char* Wt = W + woff[tile];
+    int col_next = lane < 16 ? ct[lane] : 0;  // column ids one group ahead
+    if (!debug_no_copies) {  // test hook: no stage is ever filled, so the waits for them expire
       for (; g < ng; g++) {
+        const int col = col_next;
+        if (g + 1 < ng && lane < 16) col_next = ct[16 * (g + 1) + lane];
         const int slot = g % NF_STAGES;
-        if (g >= NF_STAGES && !mbar_wait(sempty(slot), (uint32_t)((g / NF_STAGES - 1) & 1), abort_flag)) {
-          if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
-          *abort_flag = 1;
+        int ok = 1;
+        if (g >= NF_STAGES) {
+          if (lane == 0) ok = mbar_wait(sempty(slot), (uint32_t)((g / NF_STAGES - 1) & 1), abort_flag) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+        }
+        if (!ok) {
+          if (lane == 0) {
+            if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
+            *abort_flag = 1;
+          }
           break;
         }
         if (*abort_flag) break;
-        expect_tx(sfull(slot), 3u * kbytes);
-        bulk_load(ring0 + (uint32_t)slot * NF_STAGE, Wt + (int64_t)g * 3 * kbytes, 3u * kbytes, sfull(slot));
+        const uint32_t dst = ring0 + (uint32_t)slot * NF_STAGE;
+        if (lane == 0) expect_tx(sfull(slot), 3u * kbytes + 16u * NF_MCOL);
+        __syncwarp();
+        if (lane == 0) bulk_load(dst, Wt + (int64_t)g * 3 * kbytes, 3u * kbytes, sfull(slot));
+        if (lane < 16)
+          bulk_load(dst + NF_WPART + (uint32_t)lane * NF_MCOL, MPb + (int64_t)col * 384, NF_MCOL, sfull(slot));
+        __syncwarp();
       }
     }
     if (lane == 0) counts[0] = g;
@@ -277,32 +295,24 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     // slot in order: a phase parity can never alias an older phase.  The MMAs
     // complete in order, so the slot of the group's last k-step being free
     // means the other two are free as well.
-    // M of this half's 8 columns of a group, straight from L2 into registers
-    // (coalesced over the states), two groups ahead of its use (two register
-    // buffers, taken in turn)
-    const float* MPb = MP + (int64_t)sb * nn * 384 + bl;
-    const int32_t* cth = ct + 8 * h;
-    auto load_group = [&](int g, float(&dst)[3][8]) {
-      const int32_t* c = cth + 16 * g;
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const float* m = MPb + (int64_t)__ldg(c + k) * 384;
-#pragma unroll
-        for (int cc = 0; cc < 3; cc++) dst[cc][k] = __ldg(m + cc * 128);
+    for (int g = 0; g < ng && !bad; g++) {
+      const int slot = g % NF_STAGES, ks0 = 3 * g;
+      if (!wait_warp(sfull(slot), (uint32_t)((g / NF_STAGES) & 1))) {
+        bad = true;
+        break;
       }
-    };
-    auto group = [&](int g, float(&buf)[3][8]) {
-      const int ks0 = 3 * g;
+      const float* mst = (const float*)(sm + (size_t)slot * NF_STAGE + NF_WPART) + 8 * h * 384;  // [column][c][128]
       float v[3][8];
 #pragma unroll
       for (int k = 0; k < 8; k++)
 #pragma unroll
-        for (int cc = 0; cc < 3; cc++) v[cc][k] = buf[cc][k] - mbar[cc];
-      if (g + 2 < ng) load_group(g + 2, buf);
+        for (int cc = 0; cc < 3; cc++) v[cc][k] = mst[(k * 3 + cc) * 128 + bl] - mbar[cc];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sempty(slot));  // this warp has read the stage's M
       const int kl = ks0 + 2;
       if (kl >= NF_RING && !wait_warp(aempty(kl % NF_RING), (uint32_t)((kl / NF_RING - 1) & 1))) {
         bad = true;  // the MMAs of k-step kl - NF_RING have not read its slot
-        return;
+        break;
       }
       fence_after();
 #pragma unroll
@@ -323,13 +333,6 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       const int c = kl / NF_CHUNK;
       if (kl - c * NF_CHUNK >= NF_PROMOTE_AT)
         while (!bad && promoted < c) promote(promoted);
-    };
-    float va[3][8], vb[3][8];
-    load_group(0, va);
-    if (ng > 1) load_group(1, vb);
-    for (int g = 0; g < ng && !bad; g += 2) {
-      group(g, va);
-      if (g + 1 < ng && !bad) group(g + 1, vb);
     }
     while (!bad && promoted < nch) promote(promoted);
     if (bad && lane == 0) {

@@ -993,6 +993,16 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     if (leaf && (nodesrc ? h_range[c].w > h_range[c].z : h_range[c].y > h_range[c].x))
       P.h_src_leaves.push_back((int32_t)c);
   }
+  // leaves holding nodes, for the leaf-wise L2P
+  {
+    std::vector<int32_t> nl;
+    for (int64_t c = 0; c < nc; c++)
+      if (h_nchild[c] == 0 && h_range[c].w > h_range[c].z) nl.push_back((int32_t)c);
+    P.n_node_leaves = (int64_t)nl.size();
+    P.node_leaves = dalloc<int32_t>(P, std::max<size_t>(nl.size(), 1));
+    DM_CUDA(cudaMemcpyAsync(P.node_leaves, nl.data(), nl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+  }
 
   P.m2l_targets = dalloc<int32_t>(P, std::max<size_t>(P.h_m2l_targets.size(), 1));
   P.p2p_targets = dalloc<int32_t>(P, std::max<size_t>(P.h_p2p_targets.size(), 1));
