@@ -59,15 +59,19 @@ __global__ void k_ghat32(const int32_t* __restrict__ leaves, const int32_t* __re
     }
 }
 
-// P2M: one block per (source leaf, 56 coefficients n, 128 states), thread =
-// state (three blocks per leaf at p = 8).  Support nodes come in chunks of 16,
-// double-buffered in shared memory by asynchronous copies (cp.async), the
-// next chunk in flight while the current one is applied: per node the 168
-// values Gt[n - e_c] the block's 56 coefficients need (0 where n_c = 0), in
-// the order of use, and M of the 128 states.  One node costs 42 broadcast
-// 16-byte reads of Gt and 3 reads of M for 168 FMAs.
-constexpr int P2M_NN = 56, P2M_NE = 16, P2M_B = 128;
-constexpr size_t P2M_SMEM = sizeof(float) * 2 * P2M_NE * (P2M_NN * 3 + 3 * P2M_B);  // two chunk buffers
+// P2M: one block per (source leaf, 56 coefficients n, 128 SPT states), 128
+// threads, thread = SPT states (bl, bl + 128; three blocks per leaf at
+// p = 8).  Support nodes come in chunks of P2M_NE, double-buffered in shared
+// memory by asynchronous copies (cp.async), the next chunk in flight while the
+// current one is applied: per node the 168 values Gt[n - e_c] the block's 56
+// coefficients need (0 where n_c = 0), in the order of use, and M of the
+// states.  One node costs 42 broadcast 16-byte reads of Gt for 168 SPT FMAs
+// (two states per thread halve the shared-memory reads per FMA).
+constexpr int P2M_NN = 56, P2M_NE = 8, P2M_B = 128;
+template <int SPT>
+constexpr size_t p2m_smem() {  // two chunk buffers
+  return sizeof(float) * 2 * P2M_NE * (P2M_NN * 3 + 3 * SPT * P2M_B);
+}
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -75,18 +79,19 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
                : "memory");
 }
 
+template <int SPT>
 __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ leaves,
                                                  const int64_t* __restrict__ sup_off,
                                                  const int32_t* __restrict__ sup_node, const float* __restrict__ G,
                                                  const float* __restrict__ Ms, int nc, int nc1, int B, float* Q) {
-  extern __shared__ __align__(16) float p2m_smem[];
-  float(*sG)[P2M_NE][P2M_NN * 3] = (float(*)[P2M_NE][P2M_NN * 3])p2m_smem;               // [2][node][(j, c)]
-  float(*sM)[P2M_NE][3][P2M_B] = (float(*)[P2M_NE][3][P2M_B])(p2m_smem + 2 * P2M_NE * P2M_NN * 3);  // [2][node][c][state]
+  constexpr int NS = SPT * P2M_B;  // states per block
+  extern __shared__ __align__(16) float p2m_smem_[];
+  float(*sG)[P2M_NE][P2M_NN * 3] = (float(*)[P2M_NE][P2M_NN * 3])p2m_smem_;        // [2][node][(j, c)]
+  float(*sM)[P2M_NE][3][NS] = (float(*)[P2M_NE][3][NS])(p2m_smem_ + 2 * P2M_NE * P2M_NN * 3);  // [2][node][c][state]
   __shared__ int six[P2M_NN * 3];
   const int32_t c = leaves[blockIdx.x];
   const int n0 = blockIdx.y * P2M_NN;
-  const int tid = threadIdx.x, b = blockIdx.z * P2M_B + tid;
-  const bool live = b < B;
+  const int tid = threadIdx.x, bb = blockIdx.z * NS;
   for (int t = tid; t < P2M_NN * 3; t += blockDim.x) {
     const int j = t / 3, comp = t - 3 * j;
     int na = 0, nb = 0, nz = 0, ix = -1;
@@ -109,16 +114,23 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
       cp_async4(&sG[buf][r][jc], ok ? G + (e0 + r) * nc1 + ix : G, ok);
     }
     for (int r = 0; r < P2M_NE; r++) {
-      const bool ok = r < ne && live;
-      const float* mp = Ms + (ok ? (int64_t)sup_node[e0 + r] * 3 * B + b : 0);
+      const int64_t node = r < ne ? sup_node[e0 + r] : 0;
 #pragma unroll
-      for (int cc = 0; cc < 3; cc++) cp_async4(&sM[buf][r][cc][tid], ok ? mp + (int64_t)cc * B : Ms, ok);
+      for (int s2 = 0; s2 < SPT; s2++) {
+        const int b = bb + s2 * P2M_B + tid;
+        const bool ok = r < ne && b < B;
+        const float* mp = Ms + (ok ? node * 3 * B + b : 0);
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) cp_async4(&sM[buf][r][cc][s2 * P2M_B + tid], ok ? mp + (int64_t)cc * B : Ms, ok);
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  float acc[P2M_NN];
+  float acc[SPT][P2M_NN];
 #pragma unroll
-  for (int j = 0; j < P2M_NN; j++) acc[j] = 0.f;
+  for (int s2 = 0; s2 < SPT; s2++)
+#pragma unroll
+    for (int j = 0; j < P2M_NN; j++) acc[s2][j] = 0.f;
   if (so < eo) stage(so, 0);
   int buf = 0;
   for (int64_t e0 = so; e0 < eo; e0 += P2M_NE, buf ^= 1) {
@@ -131,7 +143,11 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
     }
     __syncthreads();  // this chunk complete in shared memory for every thread
     for (int r = 0; r < ne; r++) {
-      const float m0 = sM[buf][r][0][tid], m1 = sM[buf][r][1][tid], m2 = sM[buf][r][2][tid];
+      float m[SPT][3];
+#pragma unroll
+      for (int s2 = 0; s2 < SPT; s2++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) m[s2][cc] = sM[buf][r][cc][s2 * P2M_B + tid];
       const float4* g4 = (const float4*)sG[buf][r];
 #pragma unroll
       for (int q = 0; q < P2M_NN * 3 / 4; q++) {
@@ -140,16 +156,21 @@ __global__ void __launch_bounds__(P2M_B) k_p2m32(const int32_t* __restrict__ lea
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           const int jc = 4 * q + u, j = jc / 3, comp = jc % 3;
-          acc[j] = fmaf(gv[u], comp == 0 ? m0 : (comp == 1 ? m1 : m2), acc[j]);
+#pragma unroll
+          for (int s2 = 0; s2 < SPT; s2++) acc[s2][j] = fmaf(gv[u], m[s2][comp], acc[s2][j]);
         }
       }
     }
     __syncthreads();  // the buffer may be refilled
   }
-  if (live)
 #pragma unroll
-    for (int j = 0; j < P2M_NN; j++)
-      if (n0 + j < nc) Q[((int64_t)c * nc + n0 + j) * B + b] = acc[j];
+  for (int s2 = 0; s2 < SPT; s2++) {
+    const int b = bb + s2 * P2M_B + tid;
+    if (b < B)
+#pragma unroll
+      for (int j = 0; j < P2M_NN; j++)
+        if (n0 + j < nc) Q[((int64_t)c * nc + n0 + j) * B + b] = acc[s2][j];
+  }
 }
 
 // M2M of one level: thread per (cell, n, state); the warp shares (cell, n), so
@@ -250,41 +271,43 @@ __global__ void __launch_bounds__(128) k_l2p32(const int32_t* __restrict__ node_
   u[i * B + b] = v0 + v1;
 }
 
-// L2P, leaf-wise: block per (leaf holding nodes, 128 states).  The leaf's local
-// expansion (nc coefficients x 128 states, 84 KB at p = 8) is staged once in
-// shared memory (coalesced over states); the nodes follow in chunks of 16:
-// their monomials s_m(z/s) are formed in shared memory ([m][16 nodes]), and
-// thread = state accumulates the 16 potentials in registers, each coefficient
-// read once per chunk and each monomial row a broadcast float4 load.
-constexpr int L2P_NCH = 16;
+// L2P, leaf-wise: block per (leaf holding nodes, 128 states), 512 threads.
+// The leaf's local expansion (nc coefficients x 128 states, 84 KB at p = 8)
+// is staged once in shared memory by asynchronous copies (coalesced over
+// states); the nodes follow in chunks of 16: their monomials s_m(z/s) are
+// formed in shared memory ([m][16 nodes]), and thread (group g, state b)
+// accumulates the potentials of nodes 4g .. 4g + 3 of the chunk, per m one
+// read of its coefficient and one broadcast float4 of monomials.
+constexpr int L2P_NCH = 16, L2P_THREADS = 512;
 
-__global__ void __launch_bounds__(128) k_l2p32_leaf(const int32_t* __restrict__ leaves, const int4* __restrict__ range,
-                                                    const int32_t* __restrict__ level,
-                                                    const double* __restrict__ nodes_s,
-                                                    const double* __restrict__ centre, double side, int nc, int B,
-                                                    const float* __restrict__ L, float* u) {
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p32_leaf(const int32_t* __restrict__ leaves,
+                                                            const int4* __restrict__ range,
+                                                            const int32_t* __restrict__ level,
+                                                            const double* __restrict__ nodes_s,
+                                                            const double* __restrict__ centre, double side, int nc,
+                                                            int B, const float* __restrict__ L, float* u) {
   extern __shared__ __align__(16) float l2p_smem[];
   float* sL = l2p_smem;                                // [m][128 states]
   float4* smono = (float4*)(l2p_smem + nc * 128);      // [m][16 nodes] as 4 float4
   const int32_t c = leaves[blockIdx.x];
   const int4 r = range[c];
-  const int tid = threadIdx.x, b = blockIdx.y * 128 + tid;
+  const int tid = threadIdx.x, bl = tid & 127, grp = tid >> 7, b = blockIdx.y * 128 + bl;
   const bool live = b < B;
-  // the tile by asynchronous 4-byte copies, all in flight at once (zero fill
-  // for states beyond B)
-  const float* Lc = L + (int64_t)c * nc * B + (live ? b : 0);
-  for (int m = 0; m < nc; m++)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(
-                     sL + m * 128 + tid)),
-                 "l"(Lc + (int64_t)m * B), "r"(live ? 4 : 0)
-                 : "memory");
-  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (grp == 0) {  // the tile by asynchronous 4-byte copies, all in flight (zero fill beyond B)
+    const float* Lc = L + (int64_t)c * nc * B + (live ? b : 0);
+    for (int m = 0; m < nc; m++)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                       sL + m * 128 + bl)),
+                   "l"(Lc + (int64_t)m * B), "r"(live ? 4 : 0)
+                   : "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  }
   const double inv_s = 1.0 / ldexp(side, -level[c]);
   float* sm = (float*)smono;
   for (int32_t i0 = r.z; i0 < r.w; i0 += L2P_NCH) {
     const int nk = min(L2P_NCH, r.w - i0);
     __syncthreads();  // sL complete (first chunk); the previous chunk's monomials are read
-    // monomials: thread t forms those of node t % 16 for m = t / 16, t / 16 + 8, ...
+    // monomials: thread t forms those of node t % 16 for m = t / 16, t / 16 + 32, ...
     {
       const int k = tid & (L2P_NCH - 1);
       float z[3] = {0.f, 0.f, 0.f};
@@ -293,7 +316,7 @@ __global__ void __launch_bounds__(128) k_l2p32_leaf(const int32_t* __restrict__ 
 #pragma unroll
         for (int a = 0; a < 3; a++) z[a] = (float)((nodes_s[3 * i + a] - centre[3 * c + a]) * inv_s);
       }
-      for (int m = tid / L2P_NCH; m < nc; m += 128 / L2P_NCH) {
+      for (int m = tid / L2P_NCH; m < nc; m += L2P_THREADS / L2P_NCH) {
         int e[3];
         mi_decode(m, e[0], e[1], e[2]);
         float v = 1.f;
@@ -303,24 +326,21 @@ __global__ void __launch_bounds__(128) k_l2p32_leaf(const int32_t* __restrict__ 
       }
     }
     __syncthreads();
-    float acc[L2P_NCH];
-#pragma unroll
-    for (int k = 0; k < L2P_NCH; k++) acc[k] = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     for (int m = 0; m < nc; m++) {
-      const float l = sL[m * 128 + tid];
-#pragma unroll
-      for (int q = 0; q < L2P_NCH / 4; q++) {
-        const float4 w = smono[m * (L2P_NCH / 4) + q];
-        acc[4 * q] = fmaf(l, w.x, acc[4 * q]);
-        acc[4 * q + 1] = fmaf(l, w.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(l, w.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(l, w.w, acc[4 * q + 3]);
-      }
+      const float l = sL[m * 128 + bl];
+      const float4 w = smono[m * (L2P_NCH / 4) + grp];
+      a0 = fmaf(l, w.x, a0);
+      a1 = fmaf(l, w.y, a1);
+      a2 = fmaf(l, w.z, a2);
+      a3 = fmaf(l, w.w, a3);
     }
     if (live) {
-#pragma unroll
-      for (int k = 0; k < L2P_NCH; k++)
-        if (k < nk) u[(int64_t)(i0 + k) * B + b] = acc[k];
+      const int k0 = 4 * grp;
+      if (k0 < nk) u[(int64_t)(i0 + k0) * B + b] = a0;
+      if (k0 + 1 < nk) u[(int64_t)(i0 + k0 + 1) * B + b] = a1;
+      if (k0 + 2 < nk) u[(int64_t)(i0 + k0 + 2) * B + b] = a2;
+      if (k0 + 3 < nk) u[(int64_t)(i0 + k0 + 3) * B + b] = a3;
     }
   }
 }
@@ -340,8 +360,8 @@ void launch_l2p32(Plan& P, int B, const float* L, float* u, cudaStream_t s) {
     attr = smem;
   }
   const dim3 grid((unsigned)P.n_node_leaves, (unsigned)((B + 127) / 128));
-  k_l2p32_leaf<<<grid, 128, smem, s>>>(P.node_leaves, P.cell_range, P.cell_level, P.nodes_s, P.cell_centre, P.side,
-                                       P.nc, B, L, u);
+  k_l2p32_leaf<<<grid, L2P_THREADS, smem, s>>>(P.node_leaves, P.cell_range, P.cell_level, P.nodes_s,
+                                               P.cell_centre, P.side, P.nc, B, L, u);
   DM_LAUNCH("k_l2p32_leaf");
 }
 
@@ -571,13 +591,24 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
   if (!P.h_src_leaves.empty()) {
     dim3 grid((unsigned)P.h_src_leaves.size(), (unsigned)((nc + P2M_NN - 1) / P2M_NN),
               (unsigned)((B + P2M_B - 1) / P2M_B));
-    static bool attr = false;
-    if (!attr) {
-      DM_CUDA(cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2M_SMEM));
-      attr = true;
+    if (B > P2M_B) {  // two states per thread
+      static bool attr2 = false;
+      if (!attr2) {
+        DM_CUDA(cudaFuncSetAttribute(k_p2m32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<2>()));
+        attr2 = true;
+      }
+      grid.z = (unsigned)((B + 2 * P2M_B - 1) / (2 * P2M_B));
+      k_p2m32<2><<<grid, P2M_B, p2m_smem<2>(), s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1,
+                                                     B, W.Q32);
+    } else {
+      static bool attr1 = false;
+      if (!attr1) {
+        DM_CUDA(cudaFuncSetAttribute(k_p2m32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<1>()));
+        attr1 = true;
+      }
+      k_p2m32<1><<<grid, P2M_B, p2m_smem<1>(), s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1,
+                                                     B, W.Q32);
     }
-    k_p2m32<<<grid, P2M_B, P2M_SMEM, s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1, B,
-                                           W.Q32);
     DM_LAUNCH("k_p2m32");
     clk.launched();
   }
