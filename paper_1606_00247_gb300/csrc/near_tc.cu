@@ -33,11 +33,12 @@
 // it.  The A operand itself never touches shared memory: the warps that own
 // the states read their M from the stage, split it into hi and lo and write it
 // straight into a ring of tensor-memory slots (tcgen05.st), from which the MMA
-// reads it.  One thread streams the stages, one thread issues the MMAs and
-// frees the slots with
-// tcgen05.commit; the state warps move finished accumulators into FP32 totals
-// (below) and at the end add the totals to u (rows are distinct nodes: no
-// atomics).
+// reads it.  One thread streams the stages (a ring of four in shared memory),
+// one thread issues the MMAs and frees the slots with tcgen05.commit; the
+// state warps move finished accumulators into FP32 totals (below) and at the
+// end add the totals to u (rows are distinct nodes: no atomics).  Tensor
+// memory holds two accumulators, the totals and an eight-slot A ring (512
+// columns), so shared memory is left to the stages.
 //
 // Every wait is bounded: on expiry the kernel records DEMAG_ERR_TIMEOUT,
 // stops issuing, waits (bounded) for its own copies and MMAs in flight, frees
@@ -51,19 +52,20 @@ namespace {
 
 using namespace tcx;
 
-constexpr int NF_RING = 16;                      // A slots in tensor memory (k-steps in flight)
+constexpr int NF_RING = 8;                       // A slots in tensor memory (k-steps in flight)
 constexpr int NF_KSTEP_MAX = 64 * NF_ROWS;       // W bytes of one k-step: 2 limbs x 128 rows x 32 B
 constexpr int NF_WPART = 3 * NF_KSTEP_MAX;       // W of one column group (x, y, z k-steps): 24 KB
 constexpr int NF_MCOL = 3 * 128 * 4;             // M of one column for one state block: 1,536 B
 constexpr int NF_STAGE = NF_WPART + 16 * NF_MCOL;  // ring slot: W and M of one column group, 48 KB
-constexpr int NF_STAGES = 3;
+constexpr int NF_STAGES = 4;
 constexpr int NF_CHUNK = 24;                     // k-steps per accumulator before it is promoted
 constexpr int NF_PROMOTE_AT = 8;                 // ... promoted after this many k-steps of the next chunk
 constexpr int NF_THREADS = 384;                  // 4 control warps + 2 x 4 state warps
-constexpr int NF_TMEM_COLS = 512;                // accumulators D0, D1 (128 columns each), A ring (16 x 16)
-constexpr int NF_RING0 = 256;
+constexpr int NF_TMEM_COLS = 512;  // accumulators D0, D1 (128 columns each), FP32 totals (128), A ring (8 x 16)
+constexpr int NF_TOT0 = 256;
+constexpr int NF_RING0 = 384;
 constexpr int NF_NBARS = 2 * NF_STAGES + 2 * NF_RING + 4 + 1;
-constexpr size_t NF_SMEM = (size_t)NF_STAGES * NF_STAGE + (size_t)NF_ROWS * 128 * 4 + 8 * NF_NBARS + 16;
+constexpr size_t NF_SMEM = (size_t)NF_STAGES * NF_STAGE + 8 * NF_NBARS + 16;
 static_assert(NF_SMEM <= 227 * 1024, "shared memory of the near-field kernel");
 
 // M per 128-state block in the layout of the kernel's copies: MP[sb][node][c][128]
@@ -95,7 +97,7 @@ __global__ void k_nf_pack_m(int64_t nn, int B, const float* __restrict__ Ms, flo
 // accumulator aligned to the larger operand, so its error grows with the
 // number of MMAs an accumulator takes.  Every NF_CHUNK k-steps the issuer
 // switches between two accumulators (D0, D1) and restarts the new one; the
-// state warps add each finished chunk into FP32 totals in shared memory
+// state warps add each finished chunk into FP32 totals in tensor memory
 // (round to nearest) while the other accumulator fills.
 __global__ void __launch_bounds__(NF_THREADS, 1)
     k_near_tc(const int32_t* __restrict__ order, const int64_t* __restrict__ woff, const int64_t* __restrict__ coff,
@@ -104,8 +106,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
               const int32_t* __restrict__ cols, const unsigned char* __restrict__ W, const float* __restrict__ MP,
               const float* __restrict__ S, int64_t nn, int B, int nsb, float* u, int* err, int debug_no_copies) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  float* tot = (float*)(sm + (size_t)NF_STAGES * NF_STAGE);  // [row][128 states]
-  uint64_t* bars = (uint64_t*)(tot + NF_ROWS * 128);
+  uint64_t* bars = (uint64_t*)(sm + (size_t)NF_STAGES * NF_STAGE);
   uint32_t* tmem_slot = (uint32_t*)(bars + NF_NBARS);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int* counts = (int*)(tmem_slot + 2);  // stages issued, stages consumed by the MMA issuer
@@ -258,10 +259,6 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       for (int cc = 0; cc < 3; cc++) mbar[cc] = m0[cc * 128];
     }
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    // this warp's rows of the totals (16-row chunks 2 i + h), zeroed by the warp that adds into them
-    for (int c0 = 16 * h; c0 < npad; c0 += 32)
-#pragma unroll
-      for (int i = 0; i < 16; i++) tot[(c0 + i) * 128 + bl] = 0.f;
     int promoted = 0;
     bool bad = false;
     auto wait_warp = [&](uint32_t bar, uint32_t parity) {
@@ -270,7 +267,8 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
     // add this warp's rows (16-row chunks 2 i + h) of accumulator chunk c into
-    // the FP32 totals (round to nearest)
+    // the FP32 totals (round to nearest), which live in tensor memory too
+    // (columns NF_TOT0 + row; the first chunk initialises them)
     auto promote = [&](int c) {
       if (!wait_warp(dfull(c & 1), (uint32_t)((c / 2) & 1))) {
         bad = true;
@@ -280,8 +278,14 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       for (int c0 = 16 * h; c0 < npad; c0 += 32) {
         uint32_t r[16];
         tmem_ld16(tmem + lane_off + 128 * (c & 1) + c0, r);
+        if (c > 0) {
+          uint32_t t[16];
+          tmem_ld16(tmem + lane_off + NF_TOT0 + c0, t);
 #pragma unroll
-        for (int i = 0; i < 16; i++) tot[(c0 + i) * 128 + bl] += __uint_as_float(r[i]);
+          for (int i = 0; i < 16; i++) r[i] = __float_as_uint(__uint_as_float(t[i]) + __uint_as_float(r[i]));
+        }
+        tmem_st16(tmem + lane_off + NF_TOT0 + c0, r);
+        tmem_wait_st();
       }
       fence_before();
       __syncwarp();
@@ -339,15 +343,22 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
       if (!*abort_flag) atomicExch(err, (int)DEMAG_ERR_TIMEOUT);
       *abort_flag = 1;
     }
-    // every state warp has added its rows of every chunk: totals -> u
-    asm volatile("bar.sync 1, 256;" ::: "memory");
-    if (!*abort_flag) {
+    // this warp's rows of the totals -> u (each row a distinct node; the
+    // warp's lanes are consecutive states, so each row's update coalesces)
+    if (!bad && !*abort_flag) {
       const int32_t* rn = rownode + tile * NF_ROWS;
-      for (int r = h; r < npad; r += 2) {
-        const int node = rn[r];
-        if (node >= 0 && live) {
-          const float* Si = S + 3ll * node;
-          u[(int64_t)node * B + b] += tot[r * 128 + bl] + (Si[0] * mbar[0] + Si[1] * mbar[1] + Si[2] * mbar[2]);
+      fence_after();
+      for (int c0 = 16 * h; c0 < npad; c0 += 32) {
+        uint32_t t[16];
+        tmem_ld16(tmem + lane_off + NF_TOT0 + c0, t);
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          const int node = rn[c0 + i];
+          if (node >= 0 && live) {
+            const float* Si = S + 3ll * node;
+            u[(int64_t)node * B + b] +=
+                __uint_as_float(t[i]) + (Si[0] * mbar[0] + Si[1] * mbar[1] + Si[2] * mbar[2]);
+          }
         }
       }
     }
