@@ -825,7 +825,10 @@ void tune_ring(Plan& P, const TcLayout& G) {
   DM_CUDA(cudaEventCreate(&a));
   DM_CUDA(cudaEventCreate(&b));
   float best = 1e30f;
-  for (int nt = 1; nt <= 2; nt++)
+  // two-target groups carry no accumulator promotion: with promotion on (the
+  // default) the tuner keeps one target per CTA, whose accuracy it must not trade
+  const int nt_max = P.tc_prom_group > 0 ? 1 : 2;
+  for (int nt = 1; nt <= nt_max; nt++)
     for (int budget : {TC_BUDGET_2, TC_BUDGET_1}) {
       if (budget == TC_BUDGET_2 && (nt == 2 || G.tmem_cols > 256)) continue;  // one CTA per SM anyway
       for (int kps = 1; kps <= std::min(G.KS, 8); kps++) {
