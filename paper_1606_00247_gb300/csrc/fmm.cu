@@ -454,7 +454,7 @@ void launch_lumped_H_out(Plan& P, int B, const double* u_s, double* u, double* H
   DM_LAUNCH("k_lumped_H_out");
 }
 
-// host/device pointer handling shared by the drivers
+// host/device pointer handling shared by the evaluation paths
 bool eval_io_begin(Plan& P, Workspace& W, const double* M, int B, double* u, double* H, const double** Md, double** ud,
                    double** Hd, cudaStream_t s) {
   const bool dev = is_device_ptr(M);

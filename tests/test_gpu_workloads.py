@@ -5,7 +5,7 @@ bench lines):
   flux-closure magnetisation plus 5 % random tilt, p = 8, theta = 0.5: the FP64
   GPU FMM against the oracle FMM on sampled target leaves computed one by one,
   and the split-BF16 tensor-core path against FP64 per state;
-* the benchmark ball (223,668 tets) with a uniform magnetisation -- smooth M
+* the 224k-tet ball (223,668 tets) with a uniform magnetisation -- smooth M
   makes the far field a sum of large cancelling dipole terms, the hardest case
   for the tensor-core M2L's accumulation.
 
