@@ -220,19 +220,34 @@ def m2l_macs(p):
     return comb(p + 6, 6)
 
 
-def m2l_tile_flops(p, precision):
+def m2l_split_degree(p):
+    """The library's default split degree of the tensor-core M2L: the products
+    with the second BF16 limb only for terms |m| + |n| <= p - 4 (p - 3 below
+    order 8)."""
+    return p - 4 if p >= 8 else p - 3
+
+
+def m2l_tile_flops(p, precision, split_all=False):
     """Flops the tensor-core M2L issues per pair and state: every k-step
     (16 BF16 or 8 TF32 values of n) is one M = 128 MMA over the rows m still
     needed at that k-step (rows of degree t need |n| < C(p - t + 3, 3)),
-    padded to 16; times 3 for split BF16."""
+    padded to 16.  Split BF16 adds the hi x lo and lo x hi MMAs over the rows
+    whose terms take the second limb (degree <= split degree - the k-step's
+    lowest |n|; every row with split_all)."""
     cnc = lambda t: 0 if t < 0 else (t + 1) * (t + 2) * (t + 3) // 6
     pad = lambda x, m: (x + m - 1) // m * m
+    deg = lambda m: next(t for t in range(p + 1) if cnc(t) > m)
     kw = 16 if precision == "bf16x3" else 8
+    sd = m2l_split_degree(p)
     total = 0
     for ks in range(pad(cnc(p), kw) // kw):
-        rows = max([cnc(t) for t in range(p + 1) if cnc(p - t) > ks * kw] or [0])
-        total += pad(rows, 16) * kw
-    return 2.0 * total * (3 if precision == "bf16x3" else 1)
+        rows = pad(max([cnc(t) for t in range(p + 1) if cnc(p - t) > ks * kw] or [0]), 16)
+        total += rows * kw
+        if precision == "bf16x3":
+            r = sd - deg(ks * kw)
+            rows2 = rows if split_all else min(pad(cnc(r), 16) if r >= 0 else 0, rows)
+            total += 2 * rows2 * kw
+    return 2.0 * total
 
 
 def alu_peak_tflops(kind, sm_mhz):
@@ -314,7 +329,8 @@ def stage_roofline(stage, stats, steps_profiled, precision, peaks, sm_mhz, tenso
                 peak = peaks.get("tf32_mma_measured") or base * (1.1 / 2.25)
                 src = ("measured TF32 tcgen05.mma (demag_measure_peak, this run)" if peaks.get("tf32_mma_measured")
                        else src + " x 1.1/2.25 nominal TF32 ratio")
-            tile_flops = m2l_tile_flops(p, precision) * stats["n_m2l"] * B / launches_per_eval
+            tile_flops = (m2l_tile_flops(p, precision, split_all=stats.get("_split_all", False)) * stats["n_m2l"] * B
+                          / launches_per_eval)
             achieved = work / per_launch_s / 1e12
             out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(key),
@@ -322,7 +338,8 @@ def stage_roofline(stage, stats, steps_profiled, precision, peaks, sm_mhz, tenso
                         "peak_source": src,
                         "note": "achieved counts algorithmic flops 2*C(p+6,6) per pair per state; executed_tflops "
                                 "counts the padded per-k-step row prefixes issued to the tensor pipe "
-                                + ("(3 BF16 MMAs per tile)" if precision == "bf16x3" else "(1 TF32 MMA per tile)")})
+                                + ("(hi x hi everywhere, hi x lo and lo x hi on the rows whose terms take the "
+                                   "second limb)" if precision == "bf16x3" else "(1 TF32 MMA per tile)")})
             return out
         achieved = work / per_launch_s / 1e12
         peak, src = _alu_peak(kind, peaks, sm_mhz)
@@ -523,6 +540,7 @@ def run_ours(args, rank, world, local_rank):
     pst = prof.stats()
     pst["_batch"] = B
     pst["near_mode"] = args.near_mode
+    pst["_split_all"] = args.m2l_split_degree < 0
     peaks = live_peaks()
     roof = roofline_for(pst, nprof, args.precision, peaks, clk.get("sm_mhz"),
                         m2l_on_tensor_cores(args.precision, B, args.m2l_table_batch))
@@ -721,6 +739,7 @@ def run_multi(args, rank, world, local_rank, w):
     pst = prof.stats()
     pst["_batch"] = B
     pst["near_mode"] = args.near_mode
+    pst["_split_all"] = args.m2l_split_degree < 0
     roof = roofline_for(pst, nprof, args.precision, measured_peaks(), clk.get("sm_mhz"),
                         m2l_on_tensor_cores(args.precision, B, args.m2l_table_batch))
     roof["scope"] = f"largest mesh of the submission ({meshes[big][1].shape[0]} tets), evaluated alone"

@@ -28,9 +28,14 @@ def test_m2l_path_choice():
 
 def test_m2l_counts():
     assert bench.m2l_macs(8) == 3003 and bench.m2l_macs(4) == 210  # C(p + 6, 6)
-    # split BF16, p = 8: k-step row prefixes 176, 64, 48, 32 and seven of 16, K = 16, three MMAs
+    # split BF16, p = 8: k-step row prefixes 176, 64, 48, 32 and seven of 16, K = 16
     rows = [176, 64, 48, 32] + [16] * 7
-    assert bench.m2l_tile_flops(8, "bf16x3") == 2.0 * sum(r * 16 for r in rows) * 3
+    assert bench.m2l_tile_flops(8, "bf16x3", split_all=True) == 2.0 * sum(r * 16 for r in rows) * 3
+    # default split degree p - 4 = 4: the second-limb rows are those of degree <= 4 - (lowest |n| of
+    # the k-step) -- 35 (pad 48), 4 (16), 1 (16) for k-steps 0-2 (lowest |n| 0, 3, 4), none after
+    rows2 = [48, 16, 16] + [0] * 8
+    assert bench.m2l_tile_flops(8, "bf16x3") == 2.0 * 16 * (sum(rows) + 2 * sum(rows2))
+    assert bench.m2l_split_degree(8) == 4 and bench.m2l_split_degree(6) == 3
 
 
 def test_roofline_record_tensor_and_alu():
