@@ -83,8 +83,8 @@ __global__ void k_nf_pack_m(int64_t nn, int B, const float* __restrict__ Ms, flo
 // One CTA per (128-state block, tile); the state blocks of a tile are
 // neighbours in launch order so the second reads the tile's W from L2.
 //   warp 0       producer: per column group one stage = the group's W (one
-//                bulk copy) and the M of its 16 columns (one bulk copy each,
-//                issued by lanes 0..15)
+//                bulk copy) and the M of its 16 columns (one bulk copy per
+//                run of consecutive node ids, issued by the run's first lane)
 //   warp 1       MMA issuer
 //   warp 2       tensor-memory allocation
 //   warps 4..11  state warps: warp 4 + 4 h + q owns tensor-memory lanes
@@ -181,8 +181,18 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
         if (lane == 0) expect_tx(sfull(slot), 3u * kbytes + 16u * NF_MCOL);
         __syncwarp();
         if (lane == 0) bulk_load(dst, Wt + (int64_t)g * 3 * kbytes, 3u * kbytes, sfull(slot));
-        if (lane < 16)
-          bulk_load(dst + NF_WPART + (uint32_t)lane * NF_MCOL, MPb + (int64_t)col * 384, NF_MCOL, sfull(slot));
+        // M of the 16 columns: one bulk copy per run of consecutive node ids
+        // (M is node-major, so a run is contiguous; Morton-sorted columns give
+        // ~2.6 runs per group)
+        const int prev = __shfl_up_sync(0xffffffffu, col, 1);
+        const bool start = lane < 16 && (lane == 0 || col != prev + 1);
+        const uint32_t starts = __ballot_sync(0xffffffffu, start) & 0xffffu;
+        if (start) {
+          const uint32_t above = starts & ~((2u << lane) - 1u);  // run starts after this lane
+          const int len = (above ? __ffs(above) - 1 : 16) - lane;
+          bulk_load(dst + NF_WPART + (uint32_t)lane * NF_MCOL, MPb + (int64_t)col * 384, (uint32_t)len * NF_MCOL,
+                    sfull(slot));
+        }
         __syncwarp();
       }
     }
