@@ -85,7 +85,19 @@ typedef struct {
                              evaluation at p = 10 with the same leaf and
                              theta; the p argument is then ignored and
                              demag_plan_stats reports the p kept.  Applied
-                             before the leaf tuning.  0..7                 */
+                             before the leaf tuning.  0..7
+                          Tuner cache: when the environment variable
+                             DEMAG_TUNE_CACHE names a file, the choices of a
+                             tuned plan (p, leaf size, M2L launch shape) are
+                             appended to it as one text line keyed by a 64-bit
+                             hash of the mesh (node coordinates and tets), of
+                             every option except profile and graph, and of
+                             the device (name, SM count, compute capability);
+                             a later plan with the same key is built from the
+                             cached choices without timing (the same plan the
+                             tuners keep).  Unparsable or out-of-range lines
+                             are skipped; a file that cannot be written only
+                             sets a warning in demag_last_error().          */
   int profile;         /* 1: time every stage of demag_eval with CUDA events
                           on the eval stream (adds one synchronisation per
                           call); read with demag_plan_stats                  */
@@ -363,6 +375,9 @@ typedef struct {
   int64_t near_bytes;    /* bytes of stored near-field coefficients read by
                             one evaluation of up to 256 states (FP64, FP32
                             or split-BF16 layout, whichever the plan holds) */
+  int tune_source;       /* 0: autotune = 0; 1: the tuners timed their
+                            candidates; 2: their choices were read from the
+                            DEMAG_TUNE_CACHE file                           */
 } demag_stats;
 
 demag_status demag_plan_stats(demag_plan plan, demag_stats* out);

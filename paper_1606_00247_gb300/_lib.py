@@ -48,7 +48,7 @@ class demag_stats(C.Structure):
                 ("stage_ms", C.c_double * DEMAG_N_STAGES), ("stage_launches", C.c_int64 * DEMAG_N_STAGES),
                 ("n_m2l_ops", C.c_int64), ("m2l_kps", C.c_int), ("m2l_ring_bytes", C.c_int),
                 ("m2l_targets_per_cta", C.c_int), ("n_near_tiles", C.c_int64), ("near_tile_cols", C.c_int64),
-                ("near_bytes", C.c_int64)]
+                ("near_bytes", C.c_int64), ("tune_source", C.c_int)]
 
 
 class demag_tree_export(C.Structure):

@@ -2,13 +2,50 @@
 // No exception crosses it: every entry point catches and returns a status.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define DEMAG_NVTX 1
+#else
+#define DEMAG_NVTX 0
+#endif
+
 namespace demag {
+
+static const char* const kStageName[DEMAG_N_STAGES] = {"demag:gather", "demag:p2m", "demag:m2m",
+                                                       "demag:m2l",    "demag:l2l", "demag:l2p",
+                                                       "demag:near_prep", "demag:p2p", "demag:h"};
+
+static uint64_t range_start(const char* name) {
+#if DEMAG_NVTX
+  return (uint64_t)nvtxRangeStartA(name);
+#else
+  (void)name;
+  return 0;
+#endif
+}
+
+static void range_end(uint64_t id) {
+#if DEMAG_NVTX
+  if (id) nvtxRangeEnd((nvtxRangeId_t)id);
+#else
+  (void)id;
+#endif
+}
+
+// an NVTX range over one entry point
+struct EntryRange {
+  uint64_t id;
+  explicit EntryRange(const char* name) : id(range_start(name)) {}
+  ~EntryRange() { range_end(id); }
+};
 
 static thread_local std::string g_last_error;
 
@@ -29,15 +66,20 @@ StageClock::StageClock(Plan& P_, cudaStream_t s_, bool allow) : P(P_), s(s_), on
     for (auto& e : ev) DM_CUDA(cudaEventCreate(&e));
 }
 StageClock::~StageClock() {
+  range_end(range);
   if (on)
     for (auto& e : ev) cudaEventDestroy(e);
 }
 void StageClock::begin(int stage) {
   cur = stage;
   used[stage] = true;
+  range_end(range);
+  range = range_start(kStageName[stage]);
   if (on) DM_CUDA(cudaEventRecord(ev[2 * stage], s));
 }
 void StageClock::end() {
+  range_end(range);
+  range = 0;
   if (on) DM_CUDA(cudaEventRecord(ev[2 * cur + 1], s));
 }
 void StageClock::finish() {
@@ -117,11 +159,21 @@ static void release_plan(demag_plan_s* P) {
   delete P;
 }
 
+// choices of the tuners (autotune bits 0-2) for one mesh, options and device
+struct TuneChoice {
+  int p = 0, leaf = 0, nt = 0, kps = 0, budget = 0;  // order, leaf size, M2L targets per CTA, k-steps, ring bytes
+};
+
 static demag_plan_s* new_plan(const demag_options& o, int64_t n_nodes, int64_t n_tets, const double* nodes,
-                              const int32_t* tets) {
+                              const int32_t* tets, const TuneChoice* preset = nullptr) {
   demag_plan_s* P = new demag_plan_s();
   try {
     P->opt = o;
+    if (preset) {
+      P->tc_preset_nt = preset->nt;
+      P->tc_preset_kps = preset->kps;
+      P->tc_preset_budget = preset->budget;
+    }
     P->p = o.p;
     P->nc = ncoef_of(o.p);
     P->nn = n_nodes;
@@ -285,6 +337,115 @@ static int tune_p(const demag_options& o, int64_t n_nodes, int64_t n_tets, const
   return chosen;
 }
 
+// ---------------------------------------------------------------------------
+// Tuner cache.  The tuners choose by timing, which costs up to ~50 s of plan
+// time on a ball of half a million tets.  With the environment variable
+// DEMAG_TUNE_CACHE naming a file, a tuned plan's choices are appended to it
+// under a key that hashes the mesh, the options and the device, and a later
+// demag_plan_create with the same key builds the plan from them without timing.
+// Every candidate plan is built deterministically, so the plan built from the
+// cached choices is the one the tuners kept.  Lines that do not parse, carry
+// another format version or hold values out of range are skipped; the last
+// valid line of a key wins.
+constexpr int TUNE_CACHE_VERSION = 1;
+
+static const char* tune_cache_path() {
+  const char* p = std::getenv("DEMAG_TUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+// FNV-1a over 64-bit words (a byte tail is zero-padded, the length appended)
+struct Fnv1a {
+  uint64_t h = 1469598103934665603ull;
+  void word(uint64_t w) { h = (h ^ w) * 1099511628211ull; }
+  void bytes(const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+      uint64_t w;
+      std::memcpy(&w, c + i, 8);
+      word(w);
+    }
+    if (i < n) {
+      uint64_t w = 0;
+      std::memcpy(&w, c + i, n - i);
+      word(w);
+    }
+    word(n);
+  }
+};
+
+template <class T>
+static void hash_array(Fnv1a& f, const T* a, int64_t n) {
+  if (is_device_ptr(a)) {
+    std::vector<T> h(n);
+    DM_CUDA(cudaMemcpy(h.data(), a, sizeof(T) * n, cudaMemcpyDeviceToHost));
+    f.bytes(h.data(), sizeof(T) * n);
+  } else {
+    f.bytes(a, sizeof(T) * n);
+  }
+}
+
+static uint64_t tune_key(const demag_options& o, int64_t n_nodes, int64_t n_tets, const double* nodes,
+                         const int32_t* tets) {
+  Fnv1a f;
+  f.word(TUNE_CACHE_VERSION);
+  int dev = 0;
+  DM_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop{};
+  DM_CUDA(cudaGetDeviceProperties(&prop, dev));
+  f.bytes(prop.name, std::strlen(prop.name));
+  f.word((uint64_t)prop.multiProcessorCount);
+  f.word((uint64_t)(prop.major * 100 + prop.minor));
+  // every option that changes what the tuners build or time (profile and graph do not)
+  const int opts[] = {o.p, o.leaf_size, o.precision, o.near_mode, o.max_batch, o.autotune, o.m2l_targets_per_cta,
+                      o.m2l_kps, o.m2l_promote, o.m2l_promote_rows, o.m2l_table_batch, o.sources, o.near_tc,
+                      o.m2l_split_degree};
+  for (int v : opts) f.word((uint64_t)(int64_t)v);
+  uint64_t th;
+  std::memcpy(&th, &o.theta, sizeof th);
+  f.word(th);
+  f.word((uint64_t)n_nodes);
+  f.word((uint64_t)n_tets);
+  hash_array(f, nodes, 3 * n_nodes);
+  hash_array(f, tets, 4 * n_tets);
+  return f.h;
+}
+
+static bool tune_cache_find(const char* path, uint64_t key, TuneChoice& c) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char tag[16];
+    int ver = 0;
+    unsigned long long k = 0;
+    TuneChoice t;
+    if (std::sscanf(line, "%15s %d %llx %d %d %d %d %d", tag, &ver, &k, &t.p, &t.leaf, &t.nt, &t.kps, &t.budget) != 8)
+      continue;
+    if (std::strcmp(tag, "demag-tune") != 0 || ver != TUNE_CACHE_VERSION || k != key) continue;
+    if (t.p < 1 || t.p > MAX_P || t.leaf < 1 || t.nt < 0 || t.nt > 2 || t.kps < 0 || t.kps > 8 || t.budget < 0 ||
+        t.budget > 227 * 1024)
+      continue;
+    c = t;
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+static void tune_cache_add(const char* path, uint64_t key, const TuneChoice& c) {
+  FILE* f = std::fopen(path, "a");  // one short line in append mode: concurrent writers do not interleave
+  if (!f) {
+    set_last_error(std::string("warning: the tuner cache ") + path + " cannot be written");
+    return;
+  }
+  std::fprintf(f, "demag-tune %d %016llx %d %d %d %d %d\n", TUNE_CACHE_VERSION, (unsigned long long)key, c.p, c.leaf,
+               c.nt, c.kps, c.budget);
+  std::fclose(f);
+}
+
 }  // namespace demag
 
 using namespace demag;
@@ -314,6 +475,7 @@ void demag_options_default(demag_options* o) {
 
 demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, int p,
                                int leaf_size, double theta, const demag_options* opt, demag_plan* out) {
+  EntryRange range_("demag_plan_create");
   set_last_error("");
   if (out) *out = nullptr;
   demag_plan_s* P = nullptr;
@@ -346,13 +508,35 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
       fail(DEMAG_ERR_INVALID_ARG, "unknown precision");
     if (o.graph != 0 && o.graph != 1) fail(DEMAG_ERR_INVALID_ARG, "graph must be 0 or 1");
     const auto t0 = std::chrono::steady_clock::now();
-    if (o.autotune & 4) {
-      o.p = tune_p(o, n_nodes, n_tets, nodes, tets);
-      o.autotune &= ~4;
+    const bool tuning = (o.autotune & 7) != 0;
+    const char* cache = tuning ? tune_cache_path() : nullptr;
+    const uint64_t key = cache ? tune_key(o, n_nodes, n_tets, nodes, tets) : 0;
+    TuneChoice hit;
+    if (cache && tune_cache_find(cache, key, hit)) {
+      demag_options oc = o;
+      if (o.autotune & 4) oc.p = hit.p;
+      if (o.autotune & 2) oc.leaf_size = hit.leaf;
+      oc.autotune &= ~4;
+      P = new_plan(oc, n_nodes, n_tets, nodes, tets, &hit);
+      P->tune_source = 2;
+    } else {
+      if (o.autotune & 4) {
+        o.p = tune_p(o, n_nodes, n_tets, nodes, tets);
+        o.autotune &= ~4;
+      }
+      P = (o.autotune & 2) ? tune_leaf(o, n_nodes, n_tets, nodes, tets) : new_plan(o, n_nodes, n_tets, nodes, tets);
+      if (tuning) {
+        P->tune_source = 1;
+        TuneChoice c;
+        c.p = P->p;
+        c.leaf = P->opt.leaf_size;
+        c.nt = P->tc_nt;
+        c.kps = P->tc_kps;
+        c.budget = P->tc_budget;
+        if (cache) tune_cache_add(cache, key, c);
+      }
     }
-    P = (o.autotune & 2) ? tune_leaf(o, n_nodes, n_tets, nodes, tets) : new_plan(o, n_nodes, n_tets, nodes, tets);
-    if (opt && (opt->autotune & 6))
-      P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (tuning) P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (o.theta >= 1.0)
       set_last_error("warning: theta >= 1, multipole expansions may not converge for accepted pairs");
     *out = P;
@@ -362,6 +546,7 @@ demag_status demag_plan_create(const double* nodes, int64_t n_nodes, const int32
 }
 
 demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream) {
+  EntryRange range_("demag_eval");
   return guarded([&] {
     if (!plan || !M || !u) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
     if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
@@ -378,6 +563,7 @@ demag_status demag_eval(demag_plan plan, const double* M, int batch, double* u, 
 }
 
 demag_status demag_eval_field(demag_plan plan, const double* M, int batch, double* u, double* H, void* cuda_stream) {
+  EntryRange range_("demag_eval_field");
   return guarded([&] {
     if (!plan || !M || !u || !H) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
     if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
@@ -413,6 +599,7 @@ demag_status demag_eval_status(demag_plan plan, void* cuda_stream) {
 
 demag_status demag_eval_multi(const demag_plan* plans, int n_plans, const double* const* M, const int* batch,
                               double* const* u, double* const* H, void* cuda_stream) {
+  EntryRange range_("demag_eval_multi");
   return guarded([&] {
     if (!plans || !M || !batch || !u || n_plans < 1) fail(DEMAG_ERR_INVALID_ARG, "NULL array or n_plans < 1");
     std::vector<Plan*> ps(n_plans);
@@ -443,6 +630,7 @@ demag_status demag_energy(demag_plan plan, const double* M, const double* H, int
 
 demag_status demag_llg_rk4(demag_plan plan, double* m, int batch, double Ms, double alpha, const double* h_ext,
                            double dt, int steps, void* cuda_stream) {
+  EntryRange range_("demag_llg_rk4");
   return guarded([&] {
     if (!plan || !m) fail(DEMAG_ERR_INVALID_ARG, "NULL pointer argument");
     if (batch < 1 || batch > plan->opt.max_batch) fail(DEMAG_ERR_INVALID_ARG, "batch must be in 1..max_batch");
@@ -501,6 +689,7 @@ demag_status demag_plan_stats(demag_plan plan, demag_stats* o) {
   o->m2l_targets_per_cta = plan->tc_ops ? plan->tc_nt : 0;
   o->n_near_tiles = plan->nf_ntiles;
   o->near_tile_cols = plan->nf_ncols;
+  o->tune_source = plan->tune_source;
   o->near_bytes = plan->nf_W ? plan->nf_wbytes
                              : (plan->W32 ? plan->n_wentries / 3 * 16
                                           : (plan->W64 ? plan->n_wentries * 8 : 0));

@@ -96,6 +96,8 @@ struct Plan {
   double lo[3] = {0, 0, 0}, side = 0, scale = 0;
   double plan_ms = 0;
   float tuned_leaf_ms = 0;  // leaf-size tuning: device time of one evaluation of max_batch states
+  int tune_source = 0;      // 0: no tuning asked, 1: tuned by timing, 2: choices read from the tuner cache
+  int tc_preset_nt = 0, tc_preset_kps = 0, tc_preset_budget = 0;  // M2L launch shape from the tuner cache
 
   // sorted geometry
   double* nodes_s = nullptr;      // nn x 3 (sorted node order)
@@ -242,7 +244,8 @@ struct Plan {
 };
 
 // Records CUDA events around the stages of one demag_eval when profiling is on
-// and counts kernel launches always.
+// and counts kernel launches always; each stage is also an NVTX range (host
+// side, seen by profilers that attach to NVTX, free otherwise).
 struct StageClock {
   Plan& P;
   cudaStream_t s;
@@ -251,6 +254,7 @@ struct StageClock {
   int launches[DEMAG_N_STAGES] = {};
   bool used[DEMAG_N_STAGES] = {};
   int cur = -1;
+  uint64_t range = 0;  // open NVTX range of the current stage (0: none)
   StageClock(Plan& P_, cudaStream_t s_, bool allow = true);
   ~StageClock();
   void begin(int stage);

@@ -983,7 +983,17 @@ void build_m2l_tc(Plan& P, const M2lKeys& K) {
   P.tc_nt = 1;
   P.tc_kps = 0;
   P.tc_budget = 0;
-  if (P.opt.autotune && P.opt.m2l_targets_per_cta == 0 && P.opt.m2l_kps == 0) tune_ring(P, G);
+  if ((P.opt.autotune & 1) && P.opt.m2l_targets_per_cta == 0 && P.opt.m2l_kps == 0) {
+    const bool preset = P.tc_preset_kps >= 1 && P.tc_preset_kps <= 8 &&
+                        (P.tc_preset_nt == 1 || (P.tc_preset_nt == 2 && P.tc_prom_group == 0));
+    if (preset) {  // a shape this tuner chose before on the same mesh and options
+      P.tc_nt = P.tc_preset_nt;
+      P.tc_kps = P.tc_preset_kps;
+      P.tc_budget = P.tc_preset_budget;
+    } else {
+      tune_ring(P, G);
+    }
+  }
   TcRing R;
   if (!current_ring(P, G, R)) fail(DEMAG_ERR_UNSUPPORTED, "no ring shape fits the tensor-core M2L");
   P.tc_nt = R.nt;
