@@ -41,7 +41,9 @@ typedef enum {
   DEMAG_ERR_OUT_OF_MEMORY = 3,  /* device allocation failed                        */
   DEMAG_ERR_CUDA = 4,           /* a CUDA runtime call failed                      */
   DEMAG_ERR_TIMEOUT = 5,        /* a bounded device wait expired                   */
-  DEMAG_ERR_UNSUPPORTED = 6     /* option combination not built                    */
+  DEMAG_ERR_UNSUPPORTED = 6,    /* option combination not built                    */
+  DEMAG_ERR_INTERNAL = 7        /* a plan's index lists failed their bounds audit
+                                   (a planner bug; demag_last_error() names the list) */
 } demag_status;
 
 /* Arithmetic of the evaluation.  DEMAG_FP64: every stage in FP64 (the
@@ -187,7 +189,9 @@ void demag_options_default(demag_options* opt);
  *           keeps ownership of its arrays.
  * Errors: DEMAG_ERR_INVALID_ARG (NULL pointers, n_nodes<4, n_tets<1, index out
  * of range, p outside 1..12, leaf_size<1, theta<=0 or non-finite, max_batch<1),
- * DEMAG_ERR_DEGENERATE_TET, DEMAG_ERR_OUT_OF_MEMORY, DEMAG_ERR_CUDA.
+ * DEMAG_ERR_DEGENERATE_TET, DEMAG_ERR_OUT_OF_MEMORY, DEMAG_ERR_CUDA,
+ * DEMAG_ERR_INTERNAL (the finished plan failed its bounds audit, see
+ * demag_plan_audit; no plan is returned).
  * theta >= 1 is accepted; demag_last_error() then warns that expansions may
  * not converge.  Runs on the current CUDA device, on its own stream, and
  * synchronises before returning. */
@@ -321,16 +325,34 @@ demag_status demag_llg_rk4(demag_plan plan, double* m, int batch, double Ms, dou
 
 demag_status demag_plan_destroy(demag_plan plan);
 
-/* Test hook for the error path of the bounded device waits (the paper has no
- * counterpart).  flags bit 0: the tensor-core near field (DEMAG_MIXED_BF16X3,
+/* Test hooks (the paper has no counterpart).
+ * flags bit 0, the error path of the bounded device waits: the tensor-core near field (DEMAG_MIXED_BF16X3,
  * near_mode = 1) issues none of its coefficient copies, so its MMA issuer's
  * bounded wait for them expires (after about a second) with no copy and no MMA
  * in flight; the kernel records DEMAG_ERR_TIMEOUT, frees its tensor memory and
  * returns.  demag_eval then returns DEMAG_ERR_TIMEOUT for host pointers, and
  * demag_eval_status reports it for device pointers; the plan and the CUDA
- * context stay usable.  flags = 0 restores normal evaluation.
+ * context stay usable.
+ * flags bit 1, the error path of the plan audit: demag_plan_audit also audits
+ * a scratch copy of the M2L source list whose last entry is set to n_cells
+ * (only the audit reads the copy; the plan's own lists are untouched), so it
+ * returns DEMAG_ERR_INTERNAL naming that entry.
+ * flags = 0 restores normal behaviour.
  * Errors: DEMAG_ERR_INVALID_ARG (NULL plan, unknown flag bits). */
 demag_status demag_plan_debug(demag_plan plan, int flags);
+
+/* Bounds audit of the plan's index lists (every list an evaluation follows
+ * into another array: node and tet permutations, cell links and ranges, the
+ * M2L and P2P lists of Sec. 3.3, support nodes, near-field columns and tile
+ * rows, M2L operator indices and groups, gradient-operator columns): each
+ * list's count against its allocation, then every entry against the range of
+ * the array it indexes, by device kernels that only read the lists.
+ * demag_plan_create runs it on every plan before returning it; this call runs
+ * it again (a plan's lists are never modified after planning).  Synchronous.
+ * Errors: DEMAG_ERR_INVALID_ARG (NULL plan), DEMAG_ERR_INTERNAL (a list failed:
+ * demag_last_error() gives the list, the first bad position and its value),
+ * DEMAG_ERR_OUT_OF_MEMORY, DEMAG_ERR_CUDA. */
+demag_status demag_plan_audit(demag_plan plan);
 
 /* Stages of demag_eval, for the per-stage timers. */
 enum {

@@ -17,6 +17,7 @@ DEMAG_ERR_OUT_OF_MEMORY = 3
 DEMAG_ERR_CUDA = 4
 DEMAG_ERR_TIMEOUT = 5
 DEMAG_ERR_UNSUPPORTED = 6
+DEMAG_ERR_INTERNAL = 7
 
 DEMAG_FP64 = 0
 DEMAG_MIXED_FP32 = 1
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = True):
         L.demag_eval_field.argtypes = [vp, vp, i32, vp, vp, vp]
         L.demag_plan_debug.restype = i32
         L.demag_plan_debug.argtypes = [vp, i32]
+        L.demag_plan_audit.restype = i32
+        L.demag_plan_audit.argtypes = [vp]
         L.demag_eval_status.restype = i32
         L.demag_eval_status.argtypes = [vp, vp]
         L.demag_eval_noalloc.restype = i32
@@ -141,8 +144,15 @@ def demag_eval_field(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):
 
 
 def demag_plan_debug(plan, flags):
-    """Test hook: bit 0 stalls the tensor-core near field so that its bounded wait expires."""
+    """Test hooks: bit 0 stalls the tensor-core near field so that its bounded wait
+    expires; bit 1 makes demag_plan_audit also audit a copy of the M2L list with one
+    entry out of range."""
     return load().demag_plan_debug(plan, flags)
+
+
+def demag_plan_audit(plan):
+    """Bounds audit of the plan's index lists (run by demag_plan_create on every plan)."""
+    return load().demag_plan_audit(plan)
 
 
 def demag_eval_noalloc(plan, M_ptr, batch, u_ptr, H_ptr, stream_ptr):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdemag.so")
 SOURCES = ["api.cu", "plan.cu", "p2p.cu", "fmm.cu", "near.cu", "near_tc.cu", "fmm32.cu", "m2l32.cu", "m2l_tc.cu", "noalloc.cu",
-           "multi.cu", "llg.cu", "peaks.cu", "field.cu"]
+           "multi.cu", "llg.cu", "peaks.cu", "field.cu", "audit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xptxas", "-warn-spills"]

@@ -572,12 +572,19 @@ demag_status demag_eval_field(demag_plan plan, const double* M, int batch, doubl
 }
 
 demag_status demag_plan_debug(demag_plan plan, int flags) {
-  if (!plan || (flags & ~1)) {
+  if (!plan || (flags & ~3)) {
     set_last_error("demag_plan_debug: NULL plan or unknown flag bits");
     return DEMAG_ERR_INVALID_ARG;
   }
   plan->debug_flags = flags;
   return DEMAG_OK;
+}
+
+demag_status demag_plan_audit(demag_plan plan) {
+  return guarded([&] {
+    if (!plan) fail(DEMAG_ERR_INVALID_ARG, "NULL plan");
+    audit_plan(*plan, (plan->debug_flags & 2) != 0);
+  });
 }
 
 demag_status demag_eval_status(demag_plan plan, void* cuda_stream) {
@@ -767,6 +774,7 @@ const char* demag_status_string(demag_status s) {
     case DEMAG_ERR_CUDA: return "CUDA error";
     case DEMAG_ERR_TIMEOUT: return "device wait timed out";
     case DEMAG_ERR_UNSUPPORTED: return "unsupported option";
+    case DEMAG_ERR_INTERNAL: return "plan audit failed";
   }
   return "unknown status";
 }

@@ -225,7 +225,7 @@ struct Plan {
   int32_t* node_iperm = nullptr;    // original -> sorted node
 
   // FP32 far-field operators (mixed precision, per-level scaled)
-  float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)  float* cell_side32 = nullptr;     // per cell side length (float)
+  float* Ghat32 = nullptr;          // n_sup x nc1: Ghat[e][m] / s_leaf^(|m|+1)
 
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
@@ -234,7 +234,7 @@ struct Plan {
   uint8_t* bnd_flag = nullptr;      // pointwise field: sorted nodes on a boundary face (on first use)
   double* field_buf = nullptr;      // pointwise field: [sorted node][3][state]
   int field_states = 0;
-  int debug_flags = 0;              // demag_plan_debug: test hooks (bit 0: near-field stall)
+  int debug_flags = 0;              // demag_plan_debug: test hooks (bit 0: near-field stall, bit 1: planted audit entry)
 
   // per-stage timers (opt.profile) and launch counts
   double stage_ms[DEMAG_N_STAGES] = {};
@@ -282,6 +282,9 @@ void dfree(Plan& P, void* ptr);  // one plan buffer, before the plan is destroye
 
 // stages (defined in plan.cu / fmm.cu / p2p.cu / eval.cu)
 void build_plan(Plan& P, const double* nodes, const int32_t* tets);
+// bounds audit of every index list of the plan (audit.cu); plant: also audit a
+// copy of the M2L source list with one entry out of range (test hook)
+void audit_plan(Plan& P, bool plant = false);
 void eval_fp64(Plan& P, const double* M, int B, double* u, double* H, cudaStream_t s);
 void destroy_workspace(Plan& P);
 // pointwise field at the interior nodes (field.cu)

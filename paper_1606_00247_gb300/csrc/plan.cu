@@ -1128,6 +1128,7 @@ void build_plan(Plan& P, const double* nodes_in, const int32_t* tets_in) {
     dfree(P, P.Ghat);
     P.tet_geo = P.tet_grad = P.Ghat = nullptr;
   }
+  audit_plan(P);
   DM_CUDA(cudaStreamSynchronize(s));
   P.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -46,8 +46,9 @@ def test_options_default_and_status_strings(lib):
             o.m2l_table_batch, o.sources, o.near_tc, o.graph, o.m2l_split_degree) == (0,) * 10
     # the binding's struct matches the library's: the default fills exactly sizeof(demag_options)
     assert ctypes.sizeof(_lib.demag_options) == 16 * 4 + 8  # sixteen ints, one double
-    for s in range(7):
+    for s in range(8):
         assert _lib.demag_status_string(s)
+    assert _lib.demag_status_string(_lib.DEMAG_ERR_INTERNAL) == "plan audit failed"
     assert _lib.demag_status_string(99) == "unknown status"
 
 
@@ -57,4 +58,5 @@ def test_null_arguments_rejected_on_host(lib):
     st, h = _lib.demag_plan_create(None, 10, None, 1, 4, 32, 0.5, None)
     assert st == _lib.DEMAG_ERR_INVALID_ARG and not h.value
     assert _lib.demag_plan_destroy(None) == _lib.DEMAG_ERR_INVALID_ARG
+    assert _lib.demag_plan_audit(None) == _lib.DEMAG_ERR_INVALID_ARG
     assert _lib.demag_eval(None, None, 1, None, None, None) == _lib.DEMAG_ERR_INVALID_ARG
