@@ -48,4 +48,4 @@ def test_expired_wait_is_reported_and_the_plan_recovers():
     u2, H2 = plan.eval(M)
     assert _lib.demag_eval_status(plan.handle, stream) == _lib.DEMAG_OK
     assert torch.equal(u2, u_ok) and torch.equal(H2, H_ok)
-    assert _lib.demag_plan_debug(plan.handle, 2) == _lib.DEMAG_ERR_INVALID_ARG
+    assert _lib.demag_plan_debug(plan.handle, 4) == _lib.DEMAG_ERR_INVALID_ARG  # bits 0 and 1 are the hooks
