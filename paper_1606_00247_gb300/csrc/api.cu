@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -38,6 +41,18 @@ static void range_end(uint64_t id) {
 #else
   (void)id;
 #endif
+}
+
+void smem_opt_in(const void* func, size_t bytes) {
+  int dev = 0;
+  DM_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> opted;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = opted[{func, dev}];
+  if (bytes <= have) return;
+  DM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
 }
 
 // an NVTX range over one entry point

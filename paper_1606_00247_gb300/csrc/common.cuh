@@ -282,6 +282,9 @@ void dfree(Plan& P, void* ptr);  // one plan buffer, before the plan is destroye
 
 // stages (defined in plan.cu / fmm.cu / p2p.cu / eval.cu)
 void build_plan(Plan& P, const double* nodes, const int32_t* tets);
+// opt a kernel in to `bytes` of dynamic shared memory on the current device
+// (set once per kernel, device and size; thread-safe)
+void smem_opt_in(const void* func, size_t bytes);
 // bounds audit of every index list of the plan (audit.cu); plant: also audit a
 // copy of the M2L source list with one entry out of range (test hook)
 void audit_plan(Plan& P, bool plant = false);

@@ -354,11 +354,7 @@ void launch_l2p32(Plan& P, int B, const float* L, float* u, cudaStream_t s) {
     return;
   }
   if (P.n_node_leaves == 0) return;
-  static size_t attr = 0;
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_l2p32_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  smem_opt_in((const void*)k_l2p32_leaf, smem);
   const dim3 grid((unsigned)P.n_node_leaves, (unsigned)((B + 127) / 128));
   k_l2p32_leaf<<<grid, L2P_THREADS, smem, s>>>(P.node_leaves, P.cell_range, P.cell_level, P.nodes_s,
                                                P.cell_centre, P.side, P.nc, B, L, u);
@@ -592,20 +588,12 @@ void eval_mixed_ws(Plan& P, Workspace& W, const double* M, int B, double* u, dou
     dim3 grid((unsigned)P.h_src_leaves.size(), (unsigned)((nc + P2M_NN - 1) / P2M_NN),
               (unsigned)((B + P2M_B - 1) / P2M_B));
     if (B > P2M_B) {  // two states per thread
-      static bool attr2 = false;
-      if (!attr2) {
-        DM_CUDA(cudaFuncSetAttribute(k_p2m32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<2>()));
-        attr2 = true;
-      }
+      smem_opt_in((const void*)k_p2m32<2>, p2m_smem<2>());
       grid.z = (unsigned)((B + 2 * P2M_B - 1) / (2 * P2M_B));
       k_p2m32<2><<<grid, P2M_B, p2m_smem<2>(), s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1,
                                                      B, W.Q32);
     } else {
-      static bool attr1 = false;
-      if (!attr1) {
-        DM_CUDA(cudaFuncSetAttribute(k_p2m32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<1>()));
-        attr1 = true;
-      }
+      smem_opt_in((const void*)k_p2m32<1>, p2m_smem<1>());
       k_p2m32<1><<<grid, P2M_B, p2m_smem<1>(), s>>>(P.src_leaves, P.sup_off, P.sup_node, P.Ghat32, W.Ms32, nc, P.nc1,
                                                      B, W.Q32);
     }

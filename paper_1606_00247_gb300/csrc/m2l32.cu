@@ -157,11 +157,7 @@ bool launch_m2l32_fast(Plan& P, int B, const float* Q, float* L, int* err, cudaS
   const int threads = ((2 * nc + 31) / 32) * 32;
   const int chunk = (int)std::max<size_t>(1, std::min<size_t>(4, (200u << 10) / (sizeof(float) * nc * SLICE)));
   const size_t smem = sizeof(float) * (chunk * nc * SLICE + chunk * nc + chunk * 16 + chunk * 4) + sizeof(int) * nc;
-  static size_t attr = 0;
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l32_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  smem_opt_in((const void*)k_m2l32_rows, smem);
   dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((B + SLICE - 1) / SLICE));
   k_m2l32_rows<<<grid, threads, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.cell_centre, P.cell_level, P.side,
                                            P.p, nc, B, chunk, Q, L);
@@ -393,11 +389,7 @@ void launch_rc(Plan& P, int B, const float* Q, float* L, cudaStream_t s) {
   const int nthreads = std::max(32 * KS, (P.m2l_rc_nitems + 31) / 32 * 32);  // every source slot has a warp
   const size_t smem = std::max(sizeof(float) * 2 * buf_floats<SB>(P.nc) + sizeof(int) * P.nc,
                                sizeof(float) * (size_t)nthreads * SB);
-  static size_t attr = 0;
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l32_rc<CH, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  smem_opt_in((const void*)k_m2l32_rc<CH, SB>, smem);
   const dim3 grid((unsigned)P.h_m2l_targets.size(), (unsigned)((B + SB - 1) / SB));
   k_m2l32_rc<CH, SB><<<grid, nthreads, smem, s>>>(P.m2l_targets, P.m2l_off, P.m2l_src, P.m2l_tab_opdl, P.m2l_tab,
                                                   P.m2l_rc_items, P.m2l_rc_nitems, P.cell_level, P.side, P.p, P.nc, B,

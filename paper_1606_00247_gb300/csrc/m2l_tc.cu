@@ -736,12 +736,8 @@ TcLayout layout_of(const Plan& P) { return tc_layout(P.p, split_bf16(P), P.tc_ls
 
 template <int PP, bool BF16, int NT, int LS>
 void launch_fixed(Plan& P, const TcRing& R, int B, const unsigned char* QP, float* L, int* err, cudaStream_t s) {
-  static size_t attr = 0;
   const size_t smem = ring_smem(R);
-  if (smem > attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_m2l_tc<PP, BF16, NT, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  smem_opt_in((const void*)k_m2l_tc<PP, BF16, NT, LS>, smem);
   const int nsb = (B + TC_M - 1) / TC_M;
   if (NT == 1) {
     dim3 grid((unsigned)(nsb * P.h_m2l_targets.size()));

@@ -1137,11 +1137,7 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
   }
   if (B % 4 == 0) {
     const size_t smem = sizeof(float4) * NB_WARPS * 2 * NB_CW * NB_NT;  // = the reduction area
-    static bool attr3 = false;
-    if (!attr3) {
-      DM_CUDA(cudaFuncSetAttribute(k_near_apply32_v3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr3 = true;
-    }
+    smem_opt_in((const void*)k_near_apply32_v3, smem);
     dim3 grid((unsigned)nT, (unsigned)((B + NB_STATES - 1) / NB_STATES));
     k_near_apply32_v3<<<grid, NB_WARPS * 32, smem, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols,
                                                         P.w_off32, P.W32, Ms, B, u_s, err);
@@ -1149,11 +1145,7 @@ void launch_near_apply32(Plan& P, const float* Ms, int B, float* u_s, int* err, 
     return;
   }
   const size_t smem = sizeof(float4) * NA_WARPS * NA_COLS * NA_NT;
-  static bool attr = false;
-  if (!attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_near_apply32_v2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  smem_opt_in((const void*)k_near_apply32_v2, smem);
   dim3 grid((unsigned)nT, (unsigned)((B + 31) / 32));
   k_near_apply32_v2<<<grid, NA_WARPS * 32, smem, s>>>(P.p2p_targets, P.cell_range, P.w_coloff, P.w_cols, P.w_off32,
                                                       P.W32, Ms, B, u_s, err);

@@ -395,11 +395,7 @@ size_t nf_mp_floats(const Plan& P, int B) {
 
 void launch_near_tc(Plan& P, const float* Ms, float* MP, int B, float* u_s, int* err, cudaStream_t s) {
   if (P.nf_ntiles == 0) return;
-  static bool attr = false;
-  if (!attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NF_SMEM));
-    attr = true;
-  }
+  smem_opt_in((const void*)k_near_tc, NF_SMEM);
   const unsigned nsb = (unsigned)((B + 127) / 128);
   k_nf_pack_m<<<dim3((unsigned)P.nn, nsb), 128, 0, s>>>(P.nn, B, Ms, MP);
   DM_LAUNCH("k_nf_pack_m");

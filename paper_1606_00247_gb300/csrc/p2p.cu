@@ -393,11 +393,7 @@ void launch_p2p_fp64(Plan& P, const double* Ms, const double* state, int B, doub
     DM_LAUNCH("k_p2p_fp64_state");
     return;
   }
-  static bool attr = false;
-  if (!attr) {
-    DM_CUDA(cudaFuncSetAttribute(k_p2p_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PA_SMEM));
-    attr = true;
-  }
+  smem_opt_in((const void*)k_p2p_fp64, PA_SMEM);
   const dim3 grid((unsigned)nT, (unsigned)((B + PA_FS - 1) / PA_FS));
   k_p2p_fp64<<<grid, PA_WARPS * 32, PA_SMEM, s>>>(P.p2p_targets, P.cell_range, P.p2p_off, P.p2p_src, P.nodes_s,
                                              P.tets_s, P.tet_geo, P.tet_grad, Ms, B, u_s, err);
