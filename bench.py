@@ -444,6 +444,26 @@ class OracleSampler:
                 "seconds": t_up + t_tot}
 
 
+def direct_sample(nodes, tets, M1, u_fmm64=None, n=64, seed=1606):
+    """The oracle's direct sum (the plain definition of u, Eq. (2), every tet at
+    every target in closed form) at n seeded target nodes on all host cores: its
+    time extrapolated to every node, and, given the FP64 GPU FMM's u of the same
+    state, the FMM's truncation error at those nodes."""
+    import oracle
+
+    nn = nodes.shape[0]
+    tg = np.sort(np.random.default_rng(seed).choice(nn, size=min(n, nn), replace=False))
+    t0 = time.perf_counter()
+    ud = oracle.direct(nodes, tets, M1, targets=tg)
+    t = time.perf_counter() - t0
+    out = {"kind": "oracle_direct", "value": len(tg) / (t * nn), "unit": UNIT, "cores": oracle.max_threads(),
+           "sample": f"direct sum over all {tets.shape[0]} tets at {len(tg)} seeded target nodes ({t:.2f} s), "
+                     f"extrapolated to all {nn} nodes", "seconds": t}
+    if u_fmm64 is not None:
+        out["fp64_gpu_fmm_vs_direct_rel_l2"] = float(np.linalg.norm(u_fmm64[tg] - ud) / np.linalg.norm(ud))
+    return out
+
+
 def cpu_baseline(nodes, tets, w, M1, single_core=True):
     """All-thread oracle sample, plus a single-thread one (upward pass + 4 leaves)."""
     smp = OracleSampler(nodes, tets, w)
@@ -552,6 +572,7 @@ def run_ours(args, rank, world, local_rank):
     # FP64 GPU FMM of the same plan settings: throughput, and the accuracy gate
     # of the metric (rel-L2 of u and of H vs FP64, per state, every state)
     ref_info = None
+    u0_64 = u_acc[0].cpu().numpy() if args.precision == "fp64" else None
     if args.precision != "fp64" and not args.no_fp64_ref:
         nb = min(B, 16)
         p64 = Plan(nodes, tets, p=w["p"], leaf_size=w["leaf"], theta=w["theta"], precision="fp64",
@@ -560,6 +581,8 @@ def run_ours(args, rank, world, local_rank):
         for k0 in range(0, B, nb):
             kb = min(nb, B - k0)
             u64, H64 = p64.eval(M[k0:k0 + kb])
+            if k0 == 0:
+                u0_64 = u64[0].cpu().numpy()  # state 0 in FP64, for the direct-sum sample
             eu += (torch.linalg.norm(u_acc[k0:k0 + kb] - u64, dim=1) / torch.linalg.norm(u64, dim=1)).tolist()
             dh = (H_acc[k0:k0 + kb] - H64).reshape(kb, -1)
             eh += (torch.linalg.norm(dh, dim=1) / torch.linalg.norm(H64.reshape(kb, -1), dim=1)).tolist()
@@ -617,6 +640,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(nodes, tets, w, make_M(nodes.shape[0], 1, tets=tets, w=w)[0],
                                            single_core=not args.no_single_core)
+        try:  # a reference row; a failure here is recorded, it does not void the measured line
+            out["cpu_baseline"]["direct_sample"] = direct_sample(nodes, tets, M[0].cpu().numpy(), u0_64)
+        except Exception as e:  # noqa: BLE001
+            out["cpu_baseline"]["direct_sample"] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 

@@ -76,3 +76,24 @@ def test_workload_defaults_fill_batch_and_autotune():
     b = types.SimpleNamespace(workload="sphere500k", p=0, leaf=512, theta=0.0, batch=0, autotune=-1)
     w = bench.workload(b)
     assert b.autotune == 1 and w["leaf"] == 512 and w["cpu_leaf"] == 512  # a given leaf is not tuned
+
+
+def test_direct_sample_times_the_oracle_and_measures_truncation():
+    """The direct-sum reference row: the oracle's direct sum at seeded sample
+    nodes, extrapolated to all nodes; against a u that is the direct sum itself
+    the measured 'truncation' is zero, against a perturbed u it is the
+    perturbation."""
+    import numpy as np
+
+    import oracle
+    from paper_1606_00247_gb300 import inputs
+
+    nodes, tets = inputs.kuhn_box((4, 4, 4))
+    M1 = inputs.gaussian_unit_m(nodes.shape[0], batch=1)[0]
+    u = oracle.direct(nodes, tets, M1)
+    r = bench.direct_sample(nodes, tets, M1, u, n=16)
+    assert r["kind"] == "oracle_direct" and r["value"] > 0 and r["cores"] >= 1
+    assert r["fp64_gpu_fmm_vs_direct_rel_l2"] == 0.0
+    r2 = bench.direct_sample(nodes, tets, M1, u * (1 + 1e-6), n=16)
+    assert abs(r2["fp64_gpu_fmm_vs_direct_rel_l2"] - 1e-6) < 1e-12
+    assert "fp64_gpu_fmm_vs_direct_rel_l2" not in bench.direct_sample(nodes, tets, M1, None, n=4)
