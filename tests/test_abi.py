@@ -60,3 +60,42 @@ def test_null_arguments_rejected_on_host(lib):
     assert _lib.demag_plan_destroy(None) == _lib.DEMAG_ERR_INVALID_ARG
     assert _lib.demag_plan_audit(None) == _lib.DEMAG_ERR_INVALID_ARG
     assert _lib.demag_eval(None, None, 1, None, None, None) == _lib.DEMAG_ERR_INVALID_ARG
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes mirrors of demag_options, demag_stats and demag_tree_export
+    have the header's field offsets and sizes, and the binding's constants the
+    header's values (a C program built against include/demag.h prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_1606_00247_gb300 import _lib
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("demag_options", _lib.demag_options), ("demag_stats", _lib.demag_stats),
+               ("demag_tree_export", _lib.demag_tree_export)]
+    consts = [n for n in dir(_lib) if n.startswith("DEMAG_") and isinstance(getattr(_lib, n), int)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "demag.h"', "int main(void) {"]
+    for sname, st in structs:
+        lines.append(f'  printf("{sname} sizeof %zu\\n", sizeof({sname}));')
+        for fname, _ in st._fields_:
+            lines.append(f'  printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    for n in consts:
+        lines.append(f'  printf("const {n} %d\\n", (int)({n}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for sname, st in structs:
+        assert got[(sname, "sizeof")] == ctypes.sizeof(st), sname
+        for fname, _ in st._fields_:
+            assert got[(sname, fname)] == getattr(st, fname).offset, (sname, fname)
+    for n in consts:
+        assert got[("const", n)] == getattr(_lib, n), n
