@@ -13,6 +13,7 @@ from . import _lib as L
 
 _PREC = {"fp64": L.DEMAG_FP64, "fp32": L.DEMAG_MIXED_FP32, "tf32": L.DEMAG_MIXED_TF32,
          "bf16x3": L.DEMAG_MIXED_BF16X3, "bf16x6": L.DEMAG_MIXED_BF16X6}
+_SOURCES = {"tets": 0, "dipoles": 1, "patches": 2}  # DEMAG_SOURCES_TETS, _DIPOLES, _PATCHES
 
 
 def _as_f64(x, device):
@@ -49,7 +50,7 @@ class Plan:
         opt.m2l_promote = int(m2l_promote)
         opt.m2l_promote_rows = int(m2l_promote_rows)
         opt.m2l_table_batch = int(m2l_table_batch)
-        opt.sources = {"tets": 0, "dipoles": 1, "patches": 2}[sources] if isinstance(sources, str) else int(sources)
+        opt.sources = _SOURCES[sources] if isinstance(sources, str) else int(sources)
         opt.near_tc = int(near_tc)
         opt.m2l_split_degree = int(m2l_split_degree)
         opt.graph = int(bool(graph))  # demag_eval with device pointers: record once, replay as a CUDA graph

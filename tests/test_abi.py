@@ -77,12 +77,17 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     structs = [("demag_options", _lib.demag_options), ("demag_stats", _lib.demag_stats),
                ("demag_tree_export", _lib.demag_tree_export)]
     consts = [n for n in dir(_lib) if n.startswith("DEMAG_") and isinstance(getattr(_lib, n), int)]
+    # the stage order of the per-stage timers and the source models of the Python wrapper
+    stages = {f"DEMAG_STAGE_{s.upper()}": k for k, s in enumerate(_lib.STAGES)}
+    from paper_1606_00247_gb300 import api
+
+    sources = {f"DEMAG_SOURCES_{k.upper()}": v for k, v in api._SOURCES.items()}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "demag.h"', "int main(void) {"]
     for sname, st in structs:
         lines.append(f'  printf("{sname} sizeof %zu\\n", sizeof({sname}));')
         for fname, _ in st._fields_:
             lines.append(f'  printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
-    for n in consts:
+    for n in consts + list(stages) + list(sources):
         lines.append(f'  printf("const {n} %d\\n", (int)({n}));')
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
@@ -99,3 +104,5 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
             assert got[(sname, fname)] == getattr(st, fname).offset, (sname, fname)
     for n in consts:
         assert got[("const", n)] == getattr(_lib, n), n
+    for n, v in {**stages, **sources}.items():
+        assert got[("const", n)] == v, n
