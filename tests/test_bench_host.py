@@ -97,3 +97,38 @@ def test_direct_sample_times_the_oracle_and_measures_truncation():
     r2 = bench.direct_sample(nodes, tets, M1, u * (1 + 1e-6), n=16)
     assert abs(r2["fp64_gpu_fmm_vs_direct_rel_l2"] - 1e-6) < 1e-12
     assert "fp64_gpu_fmm_vs_direct_rel_l2" not in bench.direct_sample(nodes, tets, M1, None, n=4)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores) on the small
+    cube: exactly one JSON line with the contract's keys, the reference's own
+    cpu_baseline record and an e2e object that moves no bytes."""
+    import json
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "cube8",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (2, 3, 1) and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "cube8"
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 runs the oracle and prints; another rank exits 0 silently."""
+    import subprocess
+
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "cube8",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT,
+                       env=env)
+    assert r.returncode == 0 and r.stdout.strip() == "", (r.stdout[-500:], r.stderr[-1000:])
