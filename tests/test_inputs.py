@@ -56,3 +56,22 @@ def test_smoothed_states():
     raw = inputs.smoothed_unit_m(tets, nodes.shape[0], batch=3, passes=0, seed=5)
     jump = lambda x: np.mean(np.linalg.norm(x[:, e[:, 0]] - x[:, e[:, 1]], axis=-1))
     assert jump(m) < 0.6 * jump(raw)
+
+
+def test_benchmark_meshes_have_the_stated_sizes_and_fill_their_domains():
+    """The seeded meshes the workloads and the bench are quoted on: the unit cube
+    (8^3 cubes, 3072 tets), the 224k-tet ball and the 2M-tet film have the
+    stated node and tet counts, positive volumes, and volumes that add up to
+    the domain (the ball's up to the facets of its inscribed polyhedron)."""
+    nodes, tets = inputs.kuhn_box((8, 8, 8))
+    assert (nodes.shape[0], tets.shape[0]) == (729, 3072)
+    assert abs(_volumes(nodes, tets).sum() - 1.0) < 1e-12
+
+    nodes, tets = inputs.sphere(h=inputs.SPHERE_200K_H)
+    assert (nodes.shape[0], tets.shape[0]) == (35840, 223668)
+    vol = _volumes(nodes, tets)
+    assert vol.min() > 0 and abs(vol.sum() - 4.0 / 3.0 * np.pi) < 0.01 * 4.0 / 3.0 * np.pi
+
+    nodes, tets = inputs.thin_film()
+    assert (nodes.shape[0], tets.shape[0]) == (500259, 1990656)
+    assert abs(_volumes(nodes, tets).sum() / (2000.0 * 1000.0 * 10.0) - 1.0) < 1e-12
