@@ -22,6 +22,31 @@ def _as_f64(x, device):
     return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
 
 
+def _same_device(t, device):
+    return t.device.type == device.type and (device.index is None or t.device.index == device.index)
+
+
+def _check_rows(name, t, n_nodes, width):
+    """The library reads and writes (B, n_nodes[, width]) doubles through a bare
+    pointer, so a tensor of another shape is rejected here, before the call."""
+    tail = (n_nodes,) if width is None else (n_nodes, width)
+    if tuple(t.shape[-len(tail):]) != tail or t.dim() > len(tail) + 1:
+        raise ValueError(f"{name} must have shape (B, {', '.join(map(str, tail))}) or {tail}, not {tuple(t.shape)}")
+
+
+def _check_out(name, t, numel, device):
+    """A caller-given output tensor: contiguous float64 on the plan's device with
+    room for exactly the result (the library writes doubles into it)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() \
+            or t.numel() != numel or not _same_device(t, device):
+        raise ValueError(f"{name} must be a contiguous float64 tensor of {numel} elements on {device}")
+
+
+def _check_host_out(name, a, numel):
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != numel:
+        raise ValueError(f"{name} must be a C-contiguous float64 array of {numel} elements")
+
+
 def _as_i32(x, device):
     if isinstance(x, torch.Tensor):
         return x.to(device=device, dtype=torch.int32).contiguous()
@@ -38,6 +63,9 @@ class Plan:
         self.device = torch.device(device)
         nodes_t = _as_f64(nodes, self.device)
         tets_t = _as_i32(tets, self.device)
+        if nodes_t.dim() != 2 or nodes_t.shape[1] != 3 or tets_t.dim() != 2 or tets_t.shape[1] != 4:
+            raise ValueError(f"nodes must be (N_n, 3) and tets (N_t, 4), not {tuple(nodes_t.shape)} and "
+                             f"{tuple(tets_t.shape)}")
         self.n_nodes, self.n_tets = int(nodes_t.shape[0]), int(tets_t.shape[0])
         opt = L.demag_options_default()
         opt.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -80,14 +108,19 @@ class Plan:
     def eval(self, M, u=None, H=None, with_H=True, stream=None):
         """u (B, N_n) and H (B, N_n, 3) for M (B, N_n, 3) or (N_n, 3) on the device."""
         M = _as_f64(M, self.device)
+        _check_rows("M", M, self.n_nodes, 3)
         squeeze = M.dim() == 2
         if squeeze:
             M = M.unsqueeze(0)
         B = int(M.shape[0])
         if u is None:
             u = torch.empty((B, self.n_nodes), dtype=torch.float64, device=self.device)
+        else:
+            _check_out("u", u, B * self.n_nodes, self.device)
         if with_H and H is None:
             H = torch.empty((B, self.n_nodes, 3), dtype=torch.float64, device=self.device)
+        elif with_H:
+            _check_out("H", H, B * self.n_nodes * 3, self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         st = L.demag_eval(self._h, M.data_ptr(), B, u.data_ptr(), H.data_ptr() if with_H else None, s.cuda_stream)
         L.check(st, "demag_eval")
@@ -99,6 +132,7 @@ class Plan:
         """u (B, N_n) and the pointwise field H = -grad u (B, N_n, 3) at the interior
         nodes (mass-lumped H at the boundary nodes); FP64 plans with tet sources."""
         M = _as_f64(M, self.device)
+        _check_rows("M", M, self.n_nodes, 3)
         squeeze = M.dim() == 2
         if squeeze:
             M = M.unsqueeze(0)
@@ -116,6 +150,9 @@ class Plan:
             M, H = M.unsqueeze(0), H.unsqueeze(0)
         if M.dtype != torch.float64 or H.dtype != torch.float64 or not M.is_contiguous() or not H.is_contiguous():
             raise ValueError("M and H must be contiguous float64 device tensors")
+        _check_rows("M", M, self.n_nodes, 3)
+        if H.shape != M.shape:
+            raise ValueError(f"H must have M's shape {tuple(M.shape)}, not {tuple(H.shape)}")
         e = torch.empty(M.shape[0], dtype=torch.float64, device=M.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         L.check(L.demag_energy(self._h, M.data_ptr(), H.data_ptr(), M.shape[0], e.data_ptr(), s.cuda_stream),
@@ -127,6 +164,7 @@ class Plan:
         LLG equation with the demagnetising field (demag_llg_rk4, reduced units)."""
         if m.dtype != torch.float64 or not m.is_contiguous() or not m.is_cuda:
             raise ValueError("m must be a contiguous float64 device tensor")
+        _check_rows("m", m, self.n_nodes, 3)
         if m.dim() == 2:
             m = m.unsqueeze(0)
         hx = None
@@ -142,14 +180,20 @@ class Plan:
         """Same call with host (numpy) buffers: the library copies in and out.
         u and H may be given (e.g. views of pinned host memory, for fast copies)."""
         M = np.ascontiguousarray(M, dtype=np.float64)
+        if M.shape[-2:] != (self.n_nodes, 3) or M.ndim > 3:
+            raise ValueError(f"M must have shape (B, {self.n_nodes}, 3) or ({self.n_nodes}, 3), not {M.shape}")
         squeeze = M.ndim == 2
         if squeeze:
             M = M[None]
         B = M.shape[0]
         if u is None:
             u = np.empty((B, self.n_nodes))
+        else:
+            _check_host_out("u", u, B * self.n_nodes)
         if with_H and H is None:
             H = np.empty((B, self.n_nodes, 3))
+        elif with_H:
+            _check_host_out("H", H, B * self.n_nodes * 3)
         if not with_H:
             H = None
         with torch.cuda.device(self.device):
