@@ -34,12 +34,13 @@ def _check_rows(name, t, n_nodes, width):
         raise ValueError(f"{name} must have shape (B, {', '.join(map(str, tail))}) or {tail}, not {tuple(t.shape)}")
 
 
-def _check_out(name, t, numel, device):
-    """A caller-given output tensor: contiguous float64 on the plan's device with
-    room for exactly the result (the library writes doubles into it)."""
+def _check_out(name, t, numel, device=None):
+    """A caller-given output tensor: contiguous float64 (on the plan's device when
+    given) with room for exactly the result (the library writes doubles into it)."""
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() \
-            or t.numel() != numel or not _same_device(t, device):
-        raise ValueError(f"{name} must be a contiguous float64 tensor of {numel} elements on {device}")
+            or t.numel() != numel or (device is not None and not _same_device(t, device)):
+        raise ValueError(f"{name} must be a contiguous float64 tensor of {numel} elements"
+                         + (f" on {device}" if device is not None else ""))
 
 
 def _check_host_out(name, a, numel):
@@ -257,6 +258,17 @@ def eval_multi_into(plans, Ms, us, Hs=None, stream=None):
     import ctypes as C
 
     n = len(plans)
+    if n < 1 or len(Ms) != n or len(us) != n or (Hs is not None and len(Hs) != n):
+        raise ValueError("one magnetisation and one output tensor per plan")
+    for i, (pl, M) in enumerate(zip(plans, Ms)):  # shapes here; devices and batch limits in the library
+        _check_rows(f"Ms[{i}]", M, pl.n_nodes, 3)
+        if M.dim() != 3:
+            raise ValueError(f"Ms[{i}] must be (B, {pl.n_nodes}, 3): the batch is its first extent")
+        B = int(M.shape[0])
+        _check_out(f"Ms[{i}]", M, B * pl.n_nodes * 3)
+        _check_out(f"us[{i}]", us[i], B * pl.n_nodes)
+        if Hs is not None:
+            _check_out(f"Hs[{i}]", Hs[i], B * pl.n_nodes * 3)
     P = (C.c_void_p * n)(*[pl.handle for pl in plans])
     Mp = (C.c_void_p * n)(*[M.data_ptr() for M in Ms])
     up = (C.c_void_p * n)(*[u.data_ptr() for u in us])

@@ -61,3 +61,23 @@ def test_eval_host_rejects_mis_shaped_arrays():
         pl.eval_host(np.zeros((2, nn, 3)), u=np.zeros((2, nn)), H=np.zeros((2, nn, 3))[:, ::-1])
     with pytest.raises(ValueError):
         pl.eval_host(np.zeros((2, nn, 3)), u=np.zeros((2, nn + 1)))
+
+
+def test_eval_multi_into_rejects_mis_shaped_arrays():
+    from paper_1606_00247_gb300.api import eval_multi_into
+
+    a, b = _plan(5), _plan(6)
+    Ms = [torch.zeros(2, 5, 3, dtype=torch.float64), torch.zeros(1, 6, 3, dtype=torch.float64)]
+    us = [torch.zeros(2, 5, dtype=torch.float64), torch.zeros(1, 6, dtype=torch.float64)]
+    with pytest.raises(ValueError):  # counts differ
+        eval_multi_into([a, b], Ms[:1], us)
+    with pytest.raises(ValueError):  # a 2-D magnetisation has no batch extent
+        eval_multi_into([a], [torch.zeros(5, 3, dtype=torch.float64)], [torch.zeros(1, 5, dtype=torch.float64)])
+    with pytest.raises(ValueError):  # another mesh's node count
+        eval_multi_into([a, b], [Ms[1], Ms[0]], us)
+    with pytest.raises(ValueError):  # output of the wrong size
+        eval_multi_into([a, b], Ms, [us[0], torch.zeros(2, 6, dtype=torch.float64)])
+    with pytest.raises(ValueError):  # H of the wrong size
+        eval_multi_into([a, b], Ms, us, [torch.zeros(2, 5, 3, dtype=torch.float64), torch.zeros(1, 6, dtype=torch.float64)])
+    with pytest.raises(ValueError):  # single precision
+        eval_multi_into([a], [Ms[0].float()], us[:1])
