@@ -227,7 +227,7 @@ void audit_plan(Plan& P, bool plant) {
   A.values("node_perm", P.node_perm, nn, 0, nn);
   A.values("tet_perm", P.tet_perm, nt, 0, nt);
   A.values("tets_s", P.tets_s, 4 * nt, 0, nn);
-  A.values("cell_level", P.cell_level, nc, 0, 21);
+  A.values("cell_level", P.cell_level, nc, 0, MAX_LEVEL + 1);
   A.values("cell_parent", P.cell_parent, nc, -1, nc);
   A.ranges("cell_range", P.cell_range, nc);
   A.children("cell_child0", P.cell_child0, P.cell_nchild, nc);
